@@ -1,0 +1,278 @@
+"""Pins of the oracle's grid-level residual and time step against invariants, exact
+solutions and the qualitative results the paper reports (Section 7)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from riemann_exact import sample, star_state
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_cases.txt")
+
+
+def read_golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        k, v = [s.strip() for s in line.split("=", 1)]
+        out[k] = [eval(t, {}) for t in v.split()]   # numbers and simple fractions only
+    return out
+
+
+# ----------------------------------------------------------------------------- inputs
+def test_golden_matches_workloads():
+    g = read_golden()
+    for name in ("expansion", "near_vacuum", "strong"):
+        l, r, x0, t = W.SHOCK_TUBES[name]
+        assert list(l) == g[f"{name}.left"] and list(r) == g[f"{name}.right"]
+        assert x0 == g[f"{name}.x0"][0] and t == g[f"{name}.t"][0]
+    rho, p, u, v = g["quirk.left"]
+    assert (rho, u, v, p) == W.QUIRK_POST
+    rho, p, u, v = g["quirk.right"]
+    assert (rho, u, v, p) == W.QUIRK_PRE
+
+
+def test_quirk_states_are_mach6_rankine_hugoniot():
+    """The Section 7.2 states are the post-shock state of a Mach-6 shock moving into
+    (1.4, 0, 0, 1) at gamma = 1.4 (normal-shock relations in the shock frame)."""
+    M, g = 6.0, 1.4
+    rho1, u1, _, p1 = W.QUIRK_PRE
+    c1 = math.sqrt(g * p1 / rho1)
+    rho2 = rho1 * (g + 1) * M * M / ((g - 1) * M * M + 2)
+    p2 = p1 * (1 + 2 * g / (g + 1) * (M * M - 1))
+    u2 = M * c1 * (1 - rho1 / rho2)
+    assert abs(rho2 - W.QUIRK_POST[0]) < 1e-12
+    assert abs(p2 - W.QUIRK_POST[3]) < 1e-12
+    assert abs(u2 - W.QUIRK_POST[1]) < 1e-12
+
+
+def test_exact_riemann_textbook_values():
+    """The exact Riemann helper reproduces published star states (Toro 2009, Table 4.2:
+    Sod's problem and the left half of the blast wave, which is the Section 7.1.3 case)."""
+    ps, us = star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    assert abs(ps - 0.30313) < 1e-5 and abs(us - 0.92745) < 1e-5
+    ps, us = star_state((1.0, 0.0, 1000.0), (1.0, 0.0, 0.01))
+    assert abs(ps - 460.894) < 1e-3 and abs(us - 19.5975) < 1e-4
+
+
+# ----------------------------------------------------------------------------- free stream
+@pytest.mark.parametrize("recon", [0, 1, 2])
+def test_free_stream_cartesian_exact(recon):
+    spec = W.GridSpec(ni=12, nj=9, dx=0.3, dy=0.7, params=W.SchemeParams(recon=recon, m_ref=0.05))
+    U = W.free_stream(spec, u=0.31, v=-0.17)
+    assert np.all(oracle.OracleGrid(spec).residual(U) == 0.0)
+
+
+@pytest.mark.parametrize("recon", [0, 2])
+def test_free_stream_warped(recon):
+    spec = W.with_params(W.warped_periodic(16), recon=recon, m_ref=0.3)
+    U = W.free_stream(spec, u=0.31, v=-0.17)
+    R = oracle.OracleGrid(spec).residual(U)
+    # flux scale / cell volume * rounding
+    assert np.max(np.abs(R)) < 1e-12 * 1.5 / (1 / 16) ** 2 * (1 / 16)
+
+
+def test_wall_channel_free_stream():
+    """Uniform flow parallel to the S/N walls, inflow W, outflow E: R = 0 (mirror states
+    of a tangential flow reproduce it; the walls carry only pressure)."""
+    spec = W.GridSpec(ni=10, nj=6, bc=(W.INFLOW, W.OUTFLOW, W.WALL, W.WALL), inflow=(1.2, 0.8, 0.0, 0.9),
+                      params=W.SchemeParams(recon=2, m_ref=0.5))
+    U = W.free_stream(spec, 1.2, 0.8, 0.0, 0.9)
+    assert np.max(np.abs(oracle.OracleGrid(spec).residual(U))) < 1e-14
+
+
+def test_rest_state_with_solid_block_on_warped_grid():
+    spec, _ = W.warped_step(48, 16, recon=2)
+    U = W.free_stream(spec, 1.4, 0.0, 0.0, 1.0)
+    spec.bc = (W.WALL, W.WALL, W.WALL, W.WALL)
+    R = oracle.OracleGrid(spec).residual(U)
+    assert np.max(np.abs(R)) < 1e-11 * 1.0 / (3.0 / 48)
+
+
+# ----------------------------------------------------------------------------- conservation
+@pytest.mark.parametrize("case", ["cart1", "cart_muscl", "warped", "eps1"])
+def test_conservation_periodic(case):
+    if case == "warped":
+        spec = W.with_params(W.warped_periodic(16), recon=2)
+    else:
+        spec = W.GridSpec(ni=14, nj=11, dx=1 / 14, dy=1 / 11,
+                          params=W.SchemeParams(recon=0 if case == "cart1" else 1, eps1=int(case == "eps1")))
+    U = W.random_smooth_state(spec, seed=3, mach=0.8, amp=0.4)
+    g = oracle.OracleGrid(spec)
+    T0 = g.totals(U)
+    U1, _ = g.step(U, cfl=0.5, nsteps=5)
+    T1 = g.totals(U1)
+    assert np.all(np.abs(T1 - T0) <= 1e-14 * np.abs(T0).max() * 20)
+
+
+# ----------------------------------------------------------------------------- symmetry
+def _mirror_x(U):
+    V = U[:, :, ::-1].copy()
+    V[1] = -V[1]
+    return V
+
+
+@pytest.mark.parametrize("params", [dict(recon=0), dict(recon=2, eps1=1)])
+def test_mirror_symmetry(params):
+    spec = W.GridSpec(ni=12, nj=8, dx=0.1, dy=0.1, params=W.SchemeParams(m_ref=0.3, **params))
+    U = W.random_rough_state(spec, seed=7, mach=1.5)
+    Us = 0.5 * (U + _mirror_x(U))   # symmetric in x (u antisymmetric)
+    R = oracle.OracleGrid(spec).residual(Us)
+    assert np.max(np.abs(R - _mirror_x(R))) < 1e-12 * np.max(np.abs(R))
+
+
+@pytest.mark.parametrize("params", [dict(recon=0), dict(recon=1), dict(recon=2, eps1=1)])
+def test_transpose_symmetry(params):
+    """Swapping x <-> y (and u <-> v) transposes the residual: pins the y-face indexing
+    and the transposed detector stencil."""
+    spec = W.GridSpec(ni=9, nj=7, dx=0.2, dy=0.3, params=W.SchemeParams(m_ref=0.3, **params))
+    U = W.random_rough_state(spec, seed=9, mach=1.5)
+    R = oracle.OracleGrid(spec).residual(U)
+    specT = W.GridSpec(ni=7, nj=9, dx=0.3, dy=0.2, params=spec.params)
+    UT = np.stack([U[0].T, U[2].T, U[1].T, U[3].T])
+    RT = oracle.OracleGrid(specT).residual(UT)
+    expect = np.stack([R[0].T, R[2].T, R[1].T, R[3].T])
+    assert np.max(np.abs(RT - expect)) < 1e-12 * np.max(np.abs(R))
+
+
+# ----------------------------------------------------------------------------- detector
+def test_detector_brute_force():
+    """Eqs. 95-97 on a tiny periodic grid, evaluated from the definition by brute force:
+    a = min of P over the face and the four transverse faces of its two cells."""
+    spec = W.GridSpec(ni=6, nj=5, params=W.SchemeParams())
+    U = W.random_rough_state(spec, seed=17, jump=0.8)
+    rho, _, _, p = W.cons_to_prim(U)
+    ni, nj = 6, 5
+
+    def P(a, b):
+        (ia, ja), (ib, jb) = a, b
+        ra, pa = rho[ja % nj, ia % ni], p[ja % nj, ia % ni]
+        rb, pb = rho[jb % nj, ib % ni], p[jb % nj, ib % ni]
+        return min(pa / pb, pb / pa, ra / rb, rb / ra)
+
+    sx, sy = oracle.OracleGrid(spec).detector(U)
+    for j in range(nj):
+        for ic in range(ni + 1):
+            i = ic - 1
+            a = min(P((i, j), (i + 1, j)), P((i + 1, j), (i + 1, j - 1)), P((i + 1, j), (i + 1, j + 1)),
+                    P((i, j), (i, j - 1)), P((i, j), (i, j + 1)))
+            assert abs(sx[j, ic] - oracle.f(a) ** 8) < 1e-15
+    for jc in range(nj + 1):
+        for i in range(ni):
+            j = jc - 1
+            a = min(P((i, j), (i, j + 1)), P((i, j + 1), (i - 1, j + 1)), P((i, j + 1), (i + 1, j + 1)),
+                    P((i, j), (i - 1, j)), P((i, j), (i + 1, j)))
+            assert abs(sy[jc, i] - oracle.f(a) ** 8) < 1e-15
+
+
+# ----------------------------------------------------------------------------- shock tubes
+def run_tube(name, ni, cfl=0.5, ramp=False, **variant):
+    spec, U = W.shock_tube(name, ni, 2)
+    g = oracle.OracleGrid(spec, **variant)
+    tend = W.SHOCK_TUBES[name][3]
+    t, n = 0.0, 0
+    while t < tend - 1e-14:
+        c = min(cfl, 0.02 * 1.05 ** n) if ramp else cfl
+        dt = min(c / g.max_rate(U), tend - t)
+        U, _ = g.step(U, dt_fixed=dt)
+        t += dt
+        n += 1
+        rho, _, _, p = W.cons_to_prim(U)
+        if not (np.all(np.isfinite(p)) and p.min() > 0 and rho.min() > 0):
+            return None, spec
+    return U, spec
+
+
+def l1_density_error(name, U, spec):
+    l, r, x0, t = W.SHOCK_TUBES[name]
+    xc, _ = spec.cell_centres()
+    rho_ex, _, _ = sample(l, r, (xc[0] - x0) / t)
+    return float(np.mean(np.abs(U[0, 0] - rho_ex)))
+
+
+@pytest.mark.parametrize("name,ramp", [("expansion", False), ("near_vacuum", False), ("strong", True)])
+def test_shock_tube_converges_to_exact(name, ramp):
+    errs = []
+    for ni in (100, 200, 400):
+        U, spec = run_tube(name, ni, ramp=ramp, cfl=0.4 if ramp else 0.5)
+        assert U is not None, (name, ni)
+        errs.append(l1_density_error(name, U, spec))
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 0.7 * errs[0], errs
+
+
+def test_expansion_shock_removed_by_eq92():
+    """Section 7.1.1 / Fig. 3: classical Roe and Roe-AM without Eq. 92 keep an expansion
+    shock at x = 0.3; the complete Roe-AM does not."""
+    def max_jump(U):
+        return float(np.max(np.abs(np.diff(U[0, 0]))[50:70]))   # cells around x = 0.3 (ni = 200)
+    full, _ = run_tube("expansion", 200)
+    nofix, _ = run_tube("expansion", 200, ufix=0)
+    roe, _ = run_tube("expansion", 200, scheme=1)
+    assert max_jump(full) < 0.15
+    assert max_jump(nofix) > 0.5 and max_jump(roe) > 0.5
+
+
+def test_near_vacuum_positivity():
+    """Section 7.1.2: Roe-AM keeps rho, p > 0 in the near-vacuum test; classical Roe fails."""
+    U, _ = run_tube("near_vacuum", 200)
+    assert U is not None
+    U_roe, _ = run_tube("near_vacuum", 200, scheme=1)
+    assert U_roe is None
+
+
+# ----------------------------------------------------------------------------- low Mach
+def test_low_mach_residual_scaling():
+    """Section 3 asymptotics on the well-prepared Gresho vortex (p = p0 + M^2 p2): the
+    Roe-AM momentum residual stays O(1) as M -> 0, the classical Roe residual grows as 1/M
+    (the non-physical O(M) pressure mechanism that Eq. 88's f(M) removes)."""
+    res = {}
+    for scheme in (0, 1):
+        v = []
+        for M in (0.1, 0.01, 0.001):
+            spec, U = W.gresho(32, mach=M, checker=0, recon=0)
+            v.append(np.max(np.abs(oracle.OracleGrid(spec, scheme=scheme).residual(U)[1])))
+        res[scheme] = (math.log10(v[0] / v[1]), math.log10(v[1] / v[2]))
+    assert all(abs(s) < 0.05 for s in res[0]), res
+    assert all(abs(s + 1) < 0.1 for s in res[1]), res
+
+
+def test_checkerboard_mode():
+    """Section 7.6: the pure pressure checkerboard at rest is invisible to the scheme with
+    delta U_p = 0 (a stationary spurious mode); the Roe-AM delta U_p of Eq. 89 damps it
+    (energy leaves the high-pressure cells)."""
+    spec = W.GridSpec(ni=8, nj=8, dx=1 / 8, dy=1 / 8, params=W.SchemeParams(m_ref=0.01))
+    jj, ii = np.meshgrid(np.arange(8), np.arange(8), indexing="ij")
+    sign = np.where((ii + jj) % 2 == 0, 1.0, -1.0)
+    p = 1 / 1.4 + 1e-6 * sign
+    U = W.prim_to_cons(np.ones((8, 8)), 0.0, 0.0, p)
+    R0 = oracle.OracleGrid(spec, dup_mode=1).residual(U)
+    assert np.max(np.abs(R0)) < 1e-12
+    R = oracle.OracleGrid(spec).residual(U)
+    assert np.all(R[3] * sign < 0)
+
+
+# ----------------------------------------------------------------------------- vortex
+@pytest.mark.parametrize("recon,order", [(0, 0.7), (2, 1.4)])
+def test_isentropic_vortex_convergence(recon, order):
+    """Advected isentropic vortex: the error against the exact translated solution falls
+    at the expected rate (about 1 at first order, about 2 with van Leer MUSCL)."""
+    errs = []
+    tend = 1.0
+    for n in (32, 64, 128):
+        spec, U = W.isentropic_vortex(n, recon=recon)
+        g = oracle.OracleGrid(spec)
+        t = 0.0
+        while t < tend - 1e-14:
+            dt = min(0.5 / g.max_rate(U), tend - t)
+            U, _ = g.step(U, dt_fixed=dt)
+            t += dt
+        _, Ue = W.isentropic_vortex(n, t=tend, recon=recon)
+        errs.append(float(np.sqrt(np.mean((U[0] - Ue[0]) ** 2))))
+    rates = [math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])]
+    assert min(rates) > order, (errs, rates)
