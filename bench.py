@@ -1,0 +1,300 @@
+"""Benchmark of the Roe-AM SSP-RK3 step on GB300.
+
+Default workload: a batch of 512 independent periodic 2D Euler grids with seeded sizes
+from 32x32 to 512x256, free-stream Mach log-uniform in [0.001, 20] with Gaussian density
+and pressure bumps, FP32 state and flux arithmetic, first-order Roe-AM, CFL 0.5, per-grid
+dt; all grids advance in one persistent launch per Runge-Kutta stage, replayed from a
+captured CUDA graph. Metric: cell-updates per second per RK stage (whole job).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own seeded batch (weak scaling, no
+data-path collective); rank 0 prints one JSON line with the max-over-ranks time.
+`--impl reference` times the CPU oracle (the FP64 C program under oracle/) on a bounded
+sample of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Gcell-updates/s per RK stage"
+UNIT = "Gcell-updates/s"
+# Algorithmic HBM bytes per cell per RK stage in FP32 with each state read once per stage:
+# stage 1 reads U^n and writes U1 (32 B); stages 2-3 read U^(k) and U^n and write (48 B).
+BYTES_PER_CELL_STAGE = {32: (32 + 48 + 48) / 3.0, 64: 2 * (32 + 48 + 48) / 3.0}
+WORKLOAD = ("batched FP32: 512 independent periodic 2D Euler grids, sizes U{32..512} x U{32..256} (seed 20171127), "
+            "free-stream Mach 10^U(-3, log10 20) with Gaussian rho/p bumps of amplitude 0.1, first-order Roe-AM, "
+            "SSP-RK3 at CFL 0.5 with per-grid dt, one persistent launch per stage, CUDA-graph replay")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.reader.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(specs, states, steps: int = 1, budget_s: float = 20.0):
+    """Times the FP64 C oracle (single thread, as it stands) on the first grids of the batch
+    until `budget_s` is reached; returns (Gcell-updates/s per stage, sample description)."""
+    import oracle
+    cells, t_total, used = 0, 0.0, 0
+    for spec, U in zip(specs, states):
+        g = oracle.OracleGrid(spec)
+        t0 = time.perf_counter()
+        g.step(U, cfl=0.5, nsteps=steps)
+        t_total += time.perf_counter() - t0
+        cells += spec.ncells * 3 * steps
+        used += 1
+        if t_total > budget_s:
+            break
+    return cells / t_total / 1e9, f"first {used} of {len(specs)} grids of the same batch, {steps} SSP-RK3 step(s) each"
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    specs, states = W.batch(512, seed=W.DEFAULT_SEED)
+    import oracle
+    oracle.build()
+    total_cells = 0
+    times = []
+    ncores = 1
+    for it in range(args.warmup + args.steps):
+        # one step = one SSP-RK3 step of a bounded sample of the batch (about 2 s of CPU work)
+        t0 = time.perf_counter()
+        cells = 0
+        k = (it * 5) % len(specs)
+        while time.perf_counter() - t0 < 2.0:
+            s, U = specs[k], states[k]
+            oracle.OracleGrid(s).step(U, cfl=0.5)
+            cells += s.ncells * 3
+            k = (k + 1) % len(specs)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            total_cells += cells
+    value = total_cells / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "each step: consecutive grids of the batch for ~2 s, one step each"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": "FP64 C oracle, single thread, consecutive grids of the batch for ~2 s per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import paper_1711_09272_gb300 as P
+
+    prec = 32
+    specs, states = W.batch(512, seed=W.DEFAULT_SEED + rank, recon=W.RECON_FIRST)
+    ncells = sum(s.ncells for s in specs)
+    stream = torch.cuda.current_stream()
+    b = P.Batch(specs, precision=prec, device=local, cuda_stream=stream.cuda_stream)
+    packed = np.concatenate([U.ravel() for U in states])
+    b.set_state(packed, -1)
+
+    # warm-up (also captures the graph of this (cfl, dt) pair)
+    for _ in range(args.warmup):
+        b.step(cfl=0.5, nsteps=1)
+    b.step(cfl=0.5, nsteps=8)
+    b.check()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region: K steps (graph replays + direct remainder)
+    l0 = b.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        b.step(cfl=0.5, nsteps=args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = b.launches - l0
+    b.check()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    total_cells = ncells * world
+    value = total_cells * 3 * args.steps / (ms * 1e-3) / 1e9
+
+    # ---- per-launch duration of the stage kernel (events around single steps = 3 launches)
+    per = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(cfl=0.5, nsteps=1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1) / 3.0)
+    launch_ms = statistics.median(per)
+    peak, peak_kind = peaks()
+    alg_bytes = BYTES_PER_CELL_STAGE[prec] * ncells
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with pinned host buffers
+    h_in = torch.from_numpy(packed).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.roeam_set_state(b.handle, -1, h_in)
+        b.step(cfl=0.5, nsteps=1)
+        P.roeam_get_state(b.handle, -1, h_out)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = ncells * 3 / e2e_s / 1e9
+    nbytes = packed.nbytes
+
+    line = None
+    if rank == 0:
+        cpu_v, cpu_sample = (None, None)
+        if world == 1 and not args.no_cpu:
+            cpu_v, cpu_sample = cpu_baseline(specs, states, steps=1, budget_s=args.cpu_budget)
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tpath):
+            with open(tpath) as f:
+                traffic = json.load(f).get("stage_fp32_first_batch512_bytes_per_launch")
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grids_per_gpu": len(specs), "cells_per_gpu": ncells,
+                       "recon": "first order", "cfl": 0.5,
+                       "l2": "inputs larger than L2 (3 state buffers of %.0f MB each)" % (16 * ncells / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "stage_kernel<float> (fused flux + residual + RK stage)",
+                         "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec], "launch_ms": launch_ms},
+            "cpu_baseline": None if cpu_v is None else {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                                        "sample": cpu_sample},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "path": "roeam_set_state(pinned fp64) + roeam_rk_step(1) + roeam_get_state(pinned fp64)"},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

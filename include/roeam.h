@@ -1,0 +1,155 @@
+/*
+ * roeam.h — C ABI of the GB300 (sm_103a) Roe-AM finite-volume library.
+ *
+ * The library advances the 2D compressible Euler equations (the 2D form of Eq. 1 of
+ * Li, Ren & Gu, "An improved Roe scheme for all Mach-number flows simultaneously
+ * curing known problems") on structured Cartesian or curvilinear grids with the
+ * Roe-AM numerical flux of Section 6.2 (Eqs. 85-109), a cell-centred finite-volume
+ * residual and a three-stage SSP Runge-Kutta update. Every step of that path runs
+ * in the library's CUDA kernels on one GPU.
+ *
+ * Conventions used by every call:
+ *   - A handle holds a batch of `count` >= 1 independent grids that advance together.
+ *     All grids of one handle share the precision, the reconstruction order
+ *     (first order vs MUSCL) and the geometry kind (Cartesian vs curvilinear).
+ *   - Host state arrays are float64, structure of arrays, shape [4][nj][ni] with i
+ *     fastest, variables (rho, rho*u, rho*v, rho*E). With grid_idx = -1 the call
+ *     covers every grid of the batch, concatenated in grid order.
+ *   - Host arrays are owned by the caller and only read/written during the call
+ *     (the library copies them; page-locked memory makes the copies asynchronous-fast).
+ *     All device memory belongs to the handle and is released by roeam_destroy_grid.
+ *   - Calls return a status code; nothing crosses the ABI as an exception. After a
+ *     non-OK status, roeam_last_error() gives a human-readable message (thread-local).
+ *   - Errors raised on the device (non-positive or non-finite state after a step) are
+ *     reported by the next call that synchronises with the GPU (get_state,
+ *     residual_norm, conserved_totals, check, rk_step with dt_last).
+ *   - One host thread uses a handle at a time. Work is ordered on the CUDA stream
+ *     given at creation (NULL: the legacy default stream).
+ */
+#ifndef ROEAM_H
+#define ROEAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct roeam_grid roeam_grid; /* opaque batch handle */
+
+typedef enum {
+    ROEAM_OK = 0,
+    ROEAM_E_ARG = 1,          /* invalid argument (message says which) */
+    ROEAM_E_CUDA = 2,         /* a CUDA runtime call failed */
+    ROEAM_E_OOM = 3,          /* device allocation failed */
+    ROEAM_E_NONPOSITIVE = 4,  /* density or pressure <= 0 after a step */
+    ROEAM_E_NONFINITE = 5,    /* NaN or Inf in the state after a step */
+    ROEAM_E_TIMEOUT = 6,      /* a bounded device wait gave up */
+    ROEAM_E_STATE = 7         /* call not valid in the handle's current state */
+} roeam_status;
+
+enum { ROEAM_BC_PERIODIC = 0, ROEAM_BC_WALL = 1, ROEAM_BC_INFLOW = 2, ROEAM_BC_OUTFLOW = 3 };
+enum { ROEAM_RECON_FIRST = 0, ROEAM_RECON_MINMOD = 1, ROEAM_RECON_VANLEER = 2 };
+enum { ROEAM_NORM_L2 = 0, ROEAM_NORM_LINF = 1 };
+
+/* Scheme parameters (Section 6.2).
+ *   gamma    ratio of specific heats (> 1).
+ *   m_ref    global reference Mach number M_ref of Eq. 101 (> 0).
+ *   u_ref    reference speed U_ref of Eq. 108 (> 0); sets the rotated-direction threshold.
+ *   eps2     entropy-fix constant of Eqs. 102 and 112 (suggested 0.05).
+ *   eps1     0 or 1 (Eq. 111): 1 adds the entropy-fix / rotated-Riemann floor of Eq. 86.
+ *   use_s1   1 evaluates the pressure-density detector s1 of Eqs. 95-97; 0 sets s1 = 1 (Eq. 110).
+ *   recon    ROEAM_RECON_*: first order, or MUSCL on primitive variables with the minmod
+ *            or van Leer limiter (a face whose reconstructed rho or p is not positive
+ *            falls back to first order).
+ *   xi_form  0: xi of Eq. 86 with the [1 - f^8(Mbar)] factor of Eq. 68 on dU/2 (exact
+ *            full upwinding for supersonic faces, Eq. 44); 1: Eq. 86 as printed.
+ *   precision 32 (state and flux arithmetic in FP32; FP64 reductions) or 64. */
+typedef struct {
+    double gamma, m_ref, u_ref, eps2;
+    int eps1, use_s1, recon, xi_form;
+    int precision;
+    int reserved_;
+} roeam_params;
+
+/* One grid of ni x nj cells.
+ *   bc[4]      boundary type of the W (i = 0), E (i = ni-1), S (j = 0), N (j = nj-1) sides.
+ *              PERIODIC must be set on both sides of a direction. WALL mirrors the
+ *              adjacent state about the face normal; INFLOW imposes `inflow`;
+ *              OUTFLOW copies the adjacent state (zero gradient).
+ *   inflow     (rho, u, v, p) used by INFLOW sides.
+ *   xv, yv     host float64 vertex coordinates, shape [nj+1][ni+1], or both NULL for a
+ *              Cartesian grid with spacings dx, dy. For curvilinear grids dx, dy give
+ *              the uniform reference grid x = i*dx, y = j*dy that the library stores
+ *              the vertices relative to (the displacement from it is kept in the working
+ *              precision), so they should be the mean spacings.
+ *   solid      host uint8 mask [nj][ni] (1 = solid wall cell, never updated) or NULL.
+ *              Solid cells may not be combined with PERIODIC in the same direction. */
+typedef struct {
+    int ni, nj;
+    int bc[4];
+    double inflow[4];
+    const double *xv, *yv;
+    double dx, dy;
+    const uint8_t *solid;
+    roeam_params p;
+} roeam_grid_desc;
+
+/* Creates a batch handle of `count` grids on CUDA device `device`, ordering its work on
+ * `cuda_stream` (a cudaStream_t, or NULL). Copies every descriptor array. The state is
+ * zero until roeam_set_state. On success *out receives the handle. */
+roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int device, void *cuda_stream,
+                               roeam_grid **out);
+
+/* Releases the handle and all its device memory. NULL is ignored. */
+void roeam_destroy_grid(roeam_grid *g);
+
+/* Copies the conserved state of grid `grid_idx` (or all grids with -1) from the host,
+ * converting to the handle's precision, and refreshes the time-step estimate. */
+roeam_status roeam_set_state(roeam_grid *g, int grid_idx, const double *cons);
+
+/* Copies the conserved state of grid `grid_idx` (or all grids) to the host as float64.
+ * Synchronises; reports pending device errors. */
+roeam_status roeam_get_state(roeam_grid *g, int grid_idx, double *cons_out);
+
+/* Evaluates the finite-volume residual R(U) = -(1/V) sum_f F_f |S_f| (outward faces,
+ * Roe-AM flux of Eqs. 85-109) of grid `grid_idx` (or all) for the current state and
+ * copies it to res_out (same layout as the state; solid cells get 0). res_out may be
+ * NULL (the residual is then only computed). Synchronises when res_out is not NULL. */
+roeam_status roeam_flux_residual(roeam_grid *g, int grid_idx, double *res_out);
+
+/* Advances every grid by nsteps SSP-RK3 steps (Shu & Osher; each stage one fused kernel:
+ * face fluxes, residual, stage combination). Each grid's dt is dt_fixed if > 0, else
+ * cfl / max_i sum_dir (|U| + max(c, c~/theta))|S_dir| / V_i evaluated on the state at the
+ * start of the step (theta, c~ of Eqs. 99-101). dt_last (nullable, `count` doubles)
+ * receives each grid's dt of the last step (this synchronises). */
+roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_last);
+
+/* FP64 norm of the residual R(U) of grid `grid_idx` over its fluid cells, per variable:
+ * kind ROEAM_NORM_L2 gives sqrt(mean R^2), ROEAM_NORM_LINF gives max |R|. Synchronises. */
+roeam_status roeam_residual_norm(roeam_grid *g, int grid_idx, int kind, double out[4]);
+
+/* FP64 conserved totals sum_i V_i Q_i over the fluid cells of grid `grid_idx`. Synchronises. */
+roeam_status roeam_conserved_totals(roeam_grid *g, int grid_idx, double out[4]);
+
+/* Synchronises and returns the first device error recorded since the last call
+ * (ROEAM_E_NONPOSITIVE / ROEAM_E_NONFINITE), clearing it; ROEAM_OK if none. */
+roeam_status roeam_check(roeam_grid *g);
+
+/* Number of kernels this handle has launched (graph nodes count one each per replay). */
+unsigned long long roeam_launch_count(const roeam_grid *g);
+
+/* Total cells of grid `grid_idx` (or of the batch with -1), or -1 on a bad argument. */
+long long roeam_cell_count(const roeam_grid *g, int grid_idx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *roeam_last_error(void);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int roeam_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROEAM_H */

@@ -1,0 +1,647 @@
+// roeam_api.cu — host implementation of the C ABI declared in include/roeam.h.
+//
+// Owns the device memory of a batch of grids, lays the state out as pitched
+// structure-of-arrays planes, drives the fused stage kernels (directly or through a
+// cached CUDA graph of several steps), and runs the FP64 monitor reductions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "roeam.h"
+#include "roeam_internal.h"
+
+using namespace roeam;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+roeam_status fail(roeam_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                                      \
+    do {                                                                                                    \
+        cudaError_t e_ = (expr);                                                                            \
+        if (e_ != cudaSuccess)                                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? ROEAM_E_OOM : ROEAM_E_CUDA, "%s: %s (%s:%d)", #expr, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                        \
+    } while (0)
+
+long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
+
+constexpr int GRAPH_STEPS = 8;   // SSP-RK3 steps per captured graph (an even number)
+
+struct GraphKey {
+    double cfl, dt_fixed;
+    bool operator<(const GraphKey &o) const { return cfl < o.cfl || (cfl == o.cfl && dt_fixed < o.dt_fixed); }
+};
+
+}  // namespace
+
+struct roeam_grid {
+    int device = 0;
+    cudaStream_t stream = nullptr;       // user stream (work is ordered on it)
+    cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
+    int precision = 32, muscl = 0, curv = 0, count = 0;
+    size_t esize = 4;
+    int tile_cfg = 0;
+    int nblocks = 0;        // persistent CTAs of the stage kernel
+    int num_sms = 0;
+    long long total_elems = 0, total_vert = 0, total_packed = 0, total_solid = 0;
+    int max_cells = 0;
+    int total_tiles = 0;
+    std::vector<GridDev> hg;
+    std::vector<int> h_tile_base;
+    std::vector<char> state_set;
+    GridDev *d_grids = nullptr;
+    int *d_tile_base = nullptr;
+    void *U = nullptr, *A = nullptr, *B = nullptr;      // U^n (in place), stage buffers
+    void *vdx = nullptr, *vdy = nullptr;
+    uint8_t *solid = nullptr;
+    double *staging = nullptr;
+    unsigned long long *rate = nullptr;                  // 2 x count slots (double bits)
+    unsigned *status = nullptr;
+    double *partials = nullptr;
+    int partial_rows = 0;
+    double *red_out = nullptr;                           // 8 doubles
+    double *h_red = nullptr;                             // pinned 8 doubles
+    unsigned long long *h_rate = nullptr;                // pinned count
+    cudaEvent_t ev = nullptr;
+    long long step = 0;
+    unsigned long long launches = 0;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+roeam_status setup_tiles(roeam_grid *g, int cfg)
+{
+    const TileCfg tc = TILE_CFGS[cfg];
+    g->tile_cfg = cfg;
+    g->h_tile_base.assign(g->count + 1, 0);
+    int base = 0;
+    for (int k = 0; k < g->count; ++k) {
+        GridDev &G = g->hg[k];
+        G.ntx = (G.ni + tc.tx - 1) / tc.tx;
+        G.nty = (G.nj + tc.ty - 1) / tc.ty;
+        G.ntiles = G.ntx * G.nty;
+        G.tile_base = base;
+        g->h_tile_base[k] = base;
+        base += G.ntiles;
+    }
+    g->h_tile_base[g->count] = base;
+    g->total_tiles = base;
+    CUDA_TRY(cudaMemcpyAsync(g->d_grids, g->hg.data(), sizeof(GridDev) * g->count, cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->d_tile_base, g->h_tile_base.data(), sizeof(int) * (g->count + 1),
+                             cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    const int occ = g->precision == 32 ? Launchers<float>::stage_occupancy(g->muscl, g->curv, cfg)
+                                       : Launchers<double>::stage_occupancy(g->muscl, g->curv, cfg);
+    g->nblocks = std::max(1, occ * g->num_sms);
+    for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    g->graphs.clear();
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status upload_geometry(roeam_grid *g, const roeam_grid_desc *d)
+{
+    if (!g->curv) return ROEAM_OK;
+    std::vector<T> hx(g->total_vert, T(0)), hy(g->total_vert, T(0));
+    for (int k = 0; k < g->count; ++k) {
+        const GridDev &G = g->hg[k];
+        for (int J = 0; J <= G.nj; ++J)
+            for (int I = 0; I <= G.ni; ++I) {
+                const size_t s = (size_t)J * (G.ni + 1) + I;
+                const size_t t = (size_t)G.voff + (size_t)J * G.vpitch + I;
+                hx[t] = T(d[k].xv[s] - I * d[k].dx);
+                hy[t] = T(d[k].yv[s] - J * d[k].dy);
+            }
+    }
+    CUDA_TRY(cudaMemcpy(g->vdx, hx.data(), sizeof(T) * g->total_vert, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(g->vdy, hy.data(), sizeof(T) * g->total_vert, cudaMemcpyHostToDevice));
+    return ROEAM_OK;
+}
+
+// Stage-kernel arguments common to every mode.
+template <typename T>
+StageArgs<T> base_args(roeam_grid *g)
+{
+    StageArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.grids = g->d_grids;
+    a.tile_base = g->d_tile_base;
+    a.ngrids = g->count;
+    a.tile_lo = 0;
+    a.tile_hi = g->total_tiles;
+    a.vdx = (const T *)g->vdx;
+    a.vdy = (const T *)g->vdy;
+    a.solid = g->solid;
+    a.status = g->status;
+    return a;
+}
+
+template <typename T>
+roeam_status launch_step(roeam_grid *g, cudaStream_t s, long long step, double cfl, double dt_fixed)
+{
+    const int par = (int)(step & 1);
+    unsigned long long *rd = g->rate + (size_t)par * g->count;
+    unsigned long long *wr = g->rate + (size_t)(1 - par) * g->count;
+    T *U = (T *)g->U, *A = (T *)g->A, *B = (T *)g->B;
+    StageArgs<T> a = base_args<T>(g);
+    a.mode = MODE_STAGE;
+    a.rate_rd = rd;
+    a.cfl = cfl;
+    a.dt_fixed = dt_fixed;
+    // Stage 1: U1 = U^n + dt R(U^n)
+    a.src = U; a.un = U; a.dst = A; a.alpha = T(0); a.beta = T(1); a.rate_zero = wr; a.want_rate = 0;
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, s));
+    // Stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt R(U1))
+    a.src = A; a.un = U; a.dst = B; a.alpha = T(0.75); a.beta = T(0.25); a.rate_zero = nullptr;
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, s));
+    // Stage 3: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt R(U2)), in place; rate of U^{n+1} for the next dt
+    a.src = B; a.un = U; a.dst = U; a.alpha = T(1.0 / 3.0); a.beta = T(2.0 / 3.0); a.rate_wr = wr; a.want_rate = 1;
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, s));
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status refresh_rate(roeam_grid *g, int lo, int hi)
+{
+    unsigned long long *slot = g->rate + (size_t)(g->step & 1) * g->count;
+    CUDA_TRY(cudaMemsetAsync(slot + lo, 0, sizeof(unsigned long long) * (hi - lo), g->stream));
+    CUDA_TRY(Launchers<T>::rate(g->d_grids, lo, hi, (const T *)g->U, (const T *)g->vdx, (const T *)g->vdy, g->solid,
+                                slot, g->curv, g->stream));
+    g->launches += 1;
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status rk_steps(roeam_grid *g, double cfl, double dt_fixed, int nsteps)
+{
+    int left = nsteps;
+    auto direct = [&]() -> roeam_status {
+        roeam_status st = launch_step<T>(g, g->stream, g->step, cfl, dt_fixed);
+        if (st != ROEAM_OK) return st;
+        g->step += 1;
+        g->launches += 3;
+        left -= 1;
+        return ROEAM_OK;
+    };
+    if (left > 0 && (g->step & 1)) {
+        roeam_status st = direct();
+        if (st != ROEAM_OK) return st;
+    }
+    if (left >= GRAPH_STEPS) {
+        GraphKey key{cfl, dt_fixed};
+        auto it = g->graphs.find(key);
+        if (it == g->graphs.end()) {
+            cudaGraph_t graph;
+            CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (int s = 0; s < GRAPH_STEPS; ++s) {
+                roeam_status st = launch_step<T>(g, g->cap_stream, s, cfl, dt_fixed);
+                if (st != ROEAM_OK) {
+                    cudaStreamEndCapture(g->cap_stream, &graph);
+                    return st;
+                }
+            }
+            CUDA_TRY(cudaStreamEndCapture(g->cap_stream, &graph));
+            cudaGraphExec_t exec;
+            cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CUDA_TRY(e);
+            it = g->graphs.emplace(key, exec).first;
+        }
+        while (left >= GRAPH_STEPS) {
+            CUDA_TRY(cudaGraphLaunch(it->second, g->stream));
+            g->step += GRAPH_STEPS;
+            g->launches += 3 * GRAPH_STEPS;
+            left -= GRAPH_STEPS;
+        }
+    }
+    while (left > 0) {
+        roeam_status st = direct();
+        if (st != ROEAM_OK) return st;
+    }
+    return ROEAM_OK;
+}
+
+roeam_status read_status(roeam_grid *g)
+{
+    unsigned st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, g->status, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (st) {
+        CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(unsigned), g->stream));
+        if (st & ST_NONFINITE) return fail(ROEAM_E_NONFINITE, "non-finite state after a step");
+        return fail(ROEAM_E_NONPOSITIVE, "non-positive density or pressure after a step");
+    }
+    return ROEAM_OK;
+}
+
+roeam_status check_idx(const roeam_grid *g, int idx)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    if (idx < -1 || idx >= g->count) return fail(ROEAM_E_ARG, "grid_idx %d out of range [-1, %d)", idx, g->count);
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status do_set_state(roeam_grid *g, int idx, const double *cons)
+{
+    const int lo = idx < 0 ? 0 : idx, hi = idx < 0 ? g->count : idx + 1;
+    const long long p0 = g->hg[lo].poff;
+    const long long p1 = hi < g->count ? g->hg[hi].poff : g->total_packed;
+    CUDA_TRY(cudaMemcpyAsync(g->staging + p0, cons, sizeof(double) * (p1 - p0), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaEventRecord(g->ev, g->stream));
+    CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, g->staging, (T *)g->U, g->stream));
+    g->launches += 1;
+    roeam_status st = refresh_rate<T>(g, lo, hi);
+    if (st != ROEAM_OK) return st;
+    CUDA_TRY(cudaEventSynchronize(g->ev));   // the caller's array may be reused once we return
+    for (int k = lo; k < hi; ++k) g->state_set[k] = 1;
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status do_get(roeam_grid *g, int idx, const void *src, double *out)
+{
+    const int lo = idx < 0 ? 0 : idx, hi = idx < 0 ? g->count : idx + 1;
+    const long long p0 = g->hg[lo].poff;
+    const long long p1 = hi < g->count ? g->hg[hi].poff : g->total_packed;
+    CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)src, g->staging, g->stream));
+    g->launches += 1;
+    CUDA_TRY(cudaMemcpyAsync(out, g->staging + p0, sizeof(double) * (p1 - p0), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status do_residual(roeam_grid *g, int idx, double *out)
+{
+    StageArgs<T> a = base_args<T>(g);
+    a.mode = MODE_RESIDUAL;
+    a.src = (const T *)g->U;
+    a.un = (const T *)g->U;
+    a.dst = (T *)g->A;
+    if (idx >= 0) { a.tile_lo = g->h_tile_base[idx]; a.tile_hi = g->h_tile_base[idx + 1]; }
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, g->stream));
+    g->launches += 1;
+    if (out) return do_get<T>(g, idx, g->A, out);
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status do_norm(roeam_grid *g, int idx, int kind, double out[4])
+{
+    StageArgs<T> a = base_args<T>(g);
+    a.mode = MODE_NORM;
+    a.src = (const T *)g->U;
+    a.un = (const T *)g->U;
+    a.tile_lo = g->h_tile_base[idx];
+    a.tile_hi = g->h_tile_base[idx + 1];
+    a.partials = g->partials;
+    const int nb = std::min(g->nblocks, std::min(g->partial_rows, a.tile_hi - a.tile_lo));
+    CUDA_TRY(cudaMemsetAsync(g->partials, 0, sizeof(double) * 8 * g->partial_rows, g->stream));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, nb, g->stream));
+    CUDA_TRY(launch_reduce_partials(g->partials, nb, 8, g->red_out, g->stream));
+    g->launches += 2;
+    CUDA_TRY(cudaMemcpyAsync(g->h_red, g->red_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    const double nf = g->hg[idx].nfluid > 0 ? g->hg[idx].nfluid : 1.0;
+    for (int k = 0; k < 4; ++k) out[k] = kind == ROEAM_NORM_L2 ? std::sqrt(g->h_red[k] / nf) : g->h_red[4 + k];
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status do_totals(roeam_grid *g, int idx, double out[4])
+{
+    const long long n = (long long)g->hg[idx].ni * g->hg[idx].nj;
+    const int nb = (int)std::min<long long>(std::min<long long>((n + 255) / 256, 2 * g->partial_rows), 1024);
+    CUDA_TRY(Launchers<T>::totals(g->d_grids, idx, (const T *)g->U, (const T *)g->vdx, (const T *)g->vdy, g->solid,
+                                  g->partials, nb, g->curv, g->stream));
+    CUDA_TRY(launch_reduce_partials(g->partials, nb, 4, g->red_out, g->stream));
+    g->launches += 2;
+    CUDA_TRY(cudaMemcpyAsync(g->h_red, g->red_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (int k = 0; k < 4; ++k) out[k] = g->h_red[k];
+    return ROEAM_OK;
+}
+
+roeam_status validate(int count, const roeam_grid_desc *d)
+{
+    if (count < 1 || !d) return fail(ROEAM_E_ARG, "count must be >= 1 and descs non-null");
+    for (int k = 0; k < count; ++k) {
+        const roeam_grid_desc &q = d[k];
+        const roeam_params &p = q.p;
+        if (q.ni < 4 || q.nj < 4) return fail(ROEAM_E_ARG, "grid %d: ni, nj must be >= 4", k);
+        if ((long long)q.ni * q.nj > (1ll << 28)) return fail(ROEAM_E_ARG, "grid %d: too many cells", k);
+        if (!(p.gamma > 1.0)) return fail(ROEAM_E_ARG, "grid %d: gamma must be > 1", k);
+        if (!(p.m_ref > 0.0)) return fail(ROEAM_E_ARG, "grid %d: m_ref must be > 0", k);
+        if (!(p.u_ref > 0.0)) return fail(ROEAM_E_ARG, "grid %d: u_ref must be > 0", k);
+        if (!(p.eps2 >= 0.0)) return fail(ROEAM_E_ARG, "grid %d: eps2 must be >= 0", k);
+        if (p.eps1 != 0 && p.eps1 != 1) return fail(ROEAM_E_ARG, "grid %d: eps1 must be 0 or 1", k);
+        if (p.use_s1 != 0 && p.use_s1 != 1) return fail(ROEAM_E_ARG, "grid %d: use_s1 must be 0 or 1", k);
+        if (p.xi_form != 0 && p.xi_form != 1) return fail(ROEAM_E_ARG, "grid %d: xi_form must be 0 or 1", k);
+        if (p.recon < 0 || p.recon > 2) return fail(ROEAM_E_ARG, "grid %d: recon must be 0, 1 or 2", k);
+        if (p.precision != 32 && p.precision != 64) return fail(ROEAM_E_ARG, "grid %d: precision must be 32 or 64", k);
+        if (p.precision != d[0].p.precision) return fail(ROEAM_E_ARG, "grid %d: precision differs within the batch", k);
+        if ((p.recon > 0) != (d[0].p.recon > 0))
+            return fail(ROEAM_E_ARG, "grid %d: first-order and MUSCL grids cannot share a batch", k);
+        if ((q.xv != nullptr) != (q.yv != nullptr)) return fail(ROEAM_E_ARG, "grid %d: give both xv and yv or neither", k);
+        if ((q.xv != nullptr) != (d[0].xv != nullptr))
+            return fail(ROEAM_E_ARG, "grid %d: Cartesian and curvilinear grids cannot share a batch", k);
+        if (!(q.dx > 0.0) || !(q.dy > 0.0)) return fail(ROEAM_E_ARG, "grid %d: dx, dy must be > 0", k);
+        for (int s = 0; s < 4; ++s)
+            if (q.bc[s] < 0 || q.bc[s] > 3) return fail(ROEAM_E_ARG, "grid %d: bad boundary type on side %d", k, s);
+        if ((q.bc[0] == ROEAM_BC_PERIODIC) != (q.bc[1] == ROEAM_BC_PERIODIC) ||
+            (q.bc[2] == ROEAM_BC_PERIODIC) != (q.bc[3] == ROEAM_BC_PERIODIC))
+            return fail(ROEAM_E_ARG, "grid %d: PERIODIC must be set on both sides of a direction", k);
+        if (q.solid && (q.bc[0] == ROEAM_BC_PERIODIC || q.bc[2] == ROEAM_BC_PERIODIC))
+            return fail(ROEAM_E_ARG, "grid %d: solid cells cannot be combined with periodic sides", k);
+        for (int s = 0; s < 4; ++s)
+            if (q.bc[s] == ROEAM_BC_INFLOW && !(q.inflow[0] > 0.0 && q.inflow[3] > 0.0))
+                return fail(ROEAM_E_ARG, "grid %d: inflow density and pressure must be > 0", k);
+    }
+    return ROEAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *roeam_last_error(void) { return g_last_error.c_str(); }
+
+int roeam_version(void) { return 10000; }
+
+roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int device, void *cuda_stream,
+                               roeam_grid **out)
+{
+    if (!out) return fail(ROEAM_E_ARG, "out must be non-null");
+    *out = nullptr;
+    roeam_status st = validate(count, descs);
+    if (st != ROEAM_OK) return st;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(ROEAM_E_ARG, "device %d not present (%d devices)", device, ndev);
+    CUDA_TRY(cudaSetDevice(device));
+
+    roeam_grid *g = new roeam_grid();
+    g->device = device;
+    g->stream = (cudaStream_t)cuda_stream;
+    g->count = count;
+    g->precision = descs[0].p.precision;
+    g->esize = g->precision == 32 ? 4 : 8;
+    g->muscl = descs[0].p.recon > 0;
+    g->curv = descs[0].xv != nullptr;
+    CUDA_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, device));
+    g->hg.resize(count);
+    g->state_set.assign(count, 0);
+    long long off = 0, voff = 0, soff = 0, poff = 0;
+    bool any_solid = false;
+    for (int k = 0; k < count; ++k) {
+        const roeam_grid_desc &q = descs[k];
+        GridDev &G = g->hg[k];
+        std::memset(&G, 0, sizeof(G));
+        G.ni = q.ni;
+        G.nj = q.nj;
+        G.pitch = (int)round_up(q.ni, 32);
+        G.plane = (long long)q.nj * G.pitch;
+        G.off = off;
+        off += 4 * G.plane;
+        if (g->curv) {
+            G.vpitch = (int)round_up(q.ni + 1, 32);
+            G.voff = voff;
+            voff += (long long)(q.nj + 1) * G.vpitch;
+        } else {
+            G.voff = -1;
+        }
+        long long nf = (long long)q.ni * q.nj;
+        if (q.solid) {
+            G.soff = soff;
+            soff += round_up((long long)q.ni * q.nj, 256);
+            any_solid = true;
+            for (long long c = 0; c < (long long)q.ni * q.nj; ++c) nf -= q.solid[c] ? 1 : 0;
+        } else {
+            G.soff = -1;
+        }
+        G.nfluid = (double)nf;
+        G.poff = poff;
+        poff += 4ll * q.ni * q.nj;
+        g->max_cells = std::max(g->max_cells, q.ni * q.nj);
+        for (int s = 0; s < 4; ++s) G.bc[s] = q.bc[s];
+        for (int s = 0; s < 4; ++s) G.inflow[s] = q.inflow[s];
+        G.limiter = q.p.recon;
+        G.eps1 = q.p.eps1;
+        G.use_s1 = q.p.use_s1;
+        G.xi_form = q.p.xi_form;
+        G.gamma = q.p.gamma;
+        G.m_ref = q.p.m_ref;
+        G.u_ref = q.p.u_ref;
+        G.eps2 = q.p.eps2;
+        G.dx = q.dx;
+        G.dy = q.dy;
+    }
+    g->total_elems = off;
+    g->total_vert = voff;
+    g->total_packed = poff;
+    g->total_solid = soff;
+
+    auto cleanup = [&](roeam_status s) { roeam_destroy_grid(g); return s; };
+#define CREATE_TRY(expr)                                                                                        \
+    do {                                                                                                        \
+        cudaError_t e_ = (expr);                                                                                \
+        if (e_ != cudaSuccess)                                                                                  \
+            return cleanup(fail(e_ == cudaErrorMemoryAllocation ? ROEAM_E_OOM : ROEAM_E_CUDA, "%s: %s", #expr, \
+                                cudaGetErrorString(e_)));                                                       \
+    } while (0)
+
+    CREATE_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    CREATE_TRY(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));
+    CREATE_TRY(cudaMalloc(&g->d_grids, sizeof(GridDev) * count));
+    CREATE_TRY(cudaMalloc(&g->d_tile_base, sizeof(int) * (count + 1)));
+    const size_t sbytes = g->esize * (size_t)g->total_elems;
+    CREATE_TRY(cudaMalloc(&g->U, sbytes));
+    CREATE_TRY(cudaMalloc(&g->A, sbytes));
+    CREATE_TRY(cudaMalloc(&g->B, sbytes));
+    CREATE_TRY(cudaMemset(g->U, 0, sbytes));
+    CREATE_TRY(cudaMemset(g->A, 0, sbytes));
+    CREATE_TRY(cudaMemset(g->B, 0, sbytes));
+    if (g->curv) {
+        CREATE_TRY(cudaMalloc(&g->vdx, g->esize * (size_t)g->total_vert));
+        CREATE_TRY(cudaMalloc(&g->vdy, g->esize * (size_t)g->total_vert));
+    }
+    if (any_solid) {
+        CREATE_TRY(cudaMalloc(&g->solid, (size_t)g->total_solid));
+        std::vector<uint8_t> hs(g->total_solid, 0);
+        for (int k = 0; k < count; ++k)
+            if (descs[k].solid)
+                for (long long c = 0; c < (long long)descs[k].ni * descs[k].nj; ++c)
+                    hs[g->hg[k].soff + c] = descs[k].solid[c] ? 1 : 0;
+        CREATE_TRY(cudaMemcpy(g->solid, hs.data(), hs.size(), cudaMemcpyHostToDevice));
+    }
+    CREATE_TRY(cudaMalloc(&g->staging, sizeof(double) * (size_t)g->total_packed));
+    CREATE_TRY(cudaMalloc(&g->rate, sizeof(unsigned long long) * 2 * count));
+    CREATE_TRY(cudaMemset(g->rate, 0, sizeof(unsigned long long) * 2 * count));
+    CREATE_TRY(cudaMalloc(&g->status, sizeof(unsigned)));
+    CREATE_TRY(cudaMemset(g->status, 0, sizeof(unsigned)));
+    g->partial_rows = 4 * 1024;
+    CREATE_TRY(cudaMalloc(&g->partials, sizeof(double) * 8 * g->partial_rows));
+    CREATE_TRY(cudaMalloc(&g->red_out, sizeof(double) * 8));
+    CREATE_TRY(cudaMallocHost(&g->h_red, sizeof(double) * 8));
+    CREATE_TRY(cudaMallocHost(&g->h_rate, sizeof(unsigned long long) * count));
+    st = g->precision == 32 ? upload_geometry<float>(g, descs) : upload_geometry<double>(g, descs);
+    if (st != ROEAM_OK) return cleanup(st);
+    st = setup_tiles(g, 0);
+    if (st != ROEAM_OK) return cleanup(st);
+#undef CREATE_TRY
+    *out = g;
+    return ROEAM_OK;
+}
+
+void roeam_destroy_grid(roeam_grid *g)
+{
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream); else cudaDeviceSynchronize();
+    for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(g->d_grids);
+    cudaFree(g->d_tile_base);
+    cudaFree(g->U);
+    cudaFree(g->A);
+    cudaFree(g->B);
+    cudaFree(g->vdx);
+    cudaFree(g->vdy);
+    cudaFree(g->solid);
+    cudaFree(g->staging);
+    cudaFree(g->rate);
+    cudaFree(g->status);
+    cudaFree(g->partials);
+    cudaFree(g->red_out);
+    if (g->h_red) cudaFreeHost(g->h_red);
+    if (g->h_rate) cudaFreeHost(g->h_rate);
+    if (g->ev) cudaEventDestroy(g->ev);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    delete g;
+}
+
+roeam_status roeam_set_state(roeam_grid *g, int grid_idx, const double *cons)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (!cons) return fail(ROEAM_E_ARG, "cons must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    return g->precision == 32 ? do_set_state<float>(g, grid_idx, cons) : do_set_state<double>(g, grid_idx, cons);
+}
+
+roeam_status roeam_get_state(roeam_grid *g, int grid_idx, double *cons_out)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (!cons_out) return fail(ROEAM_E_ARG, "cons_out must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    st = g->precision == 32 ? do_get<float>(g, grid_idx, g->U, cons_out) : do_get<double>(g, grid_idx, g->U, cons_out);
+    if (st != ROEAM_OK) return st;
+    return read_status(g);
+}
+
+roeam_status roeam_flux_residual(roeam_grid *g, int grid_idx, double *res_out)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    for (int k = 0; k < g->count; ++k)
+        if ((grid_idx < 0 || grid_idx == k) && !g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
+    CUDA_TRY(cudaSetDevice(g->device));
+    return g->precision == 32 ? do_residual<float>(g, grid_idx, res_out) : do_residual<double>(g, grid_idx, res_out);
+}
+
+roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_last)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    if (nsteps < 0) return fail(ROEAM_E_ARG, "nsteps must be >= 0");
+    if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(ROEAM_E_ARG, "need cfl > 0 or dt_fixed > 0");
+    if (!std::isfinite(cfl) || !std::isfinite(dt_fixed)) return fail(ROEAM_E_ARG, "cfl and dt_fixed must be finite");
+    for (int k = 0; k < g->count; ++k)
+        if (!g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
+    CUDA_TRY(cudaSetDevice(g->device));
+    const long long step0 = g->step;
+    roeam_status st = g->precision == 32 ? rk_steps<float>(g, cfl, dt_fixed, nsteps)
+                                         : rk_steps<double>(g, cfl, dt_fixed, nsteps);
+    if (st != ROEAM_OK) return st;
+    if (dt_last) {
+        if (nsteps == 0 || dt_fixed > 0.0) {
+            for (int k = 0; k < g->count; ++k) dt_last[k] = nsteps == 0 ? 0.0 : dt_fixed;
+        } else {
+            const int par = (int)((step0 + nsteps - 1) & 1);   // slot the last step read its rate from
+            CUDA_TRY(cudaMemcpyAsync(g->h_rate, g->rate + (size_t)par * g->count,
+                                     sizeof(unsigned long long) * g->count, cudaMemcpyDeviceToHost, g->stream));
+            CUDA_TRY(cudaStreamSynchronize(g->stream));
+            for (int k = 0; k < g->count; ++k) {
+                double r;
+                std::memcpy(&r, g->h_rate + k, sizeof(double));
+                dt_last[k] = cfl / r;
+            }
+        }
+        return read_status(g);
+    }
+    return ROEAM_OK;
+}
+
+roeam_status roeam_residual_norm(roeam_grid *g, int grid_idx, int kind, double out[4])
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (grid_idx < 0) return fail(ROEAM_E_ARG, "residual_norm needs one grid (grid_idx >= 0)");
+    if (kind != ROEAM_NORM_L2 && kind != ROEAM_NORM_LINF) return fail(ROEAM_E_ARG, "bad norm kind %d", kind);
+    if (!out) return fail(ROEAM_E_ARG, "out must be non-null");
+    if (!g->state_set[grid_idx]) return fail(ROEAM_E_STATE, "state of grid %d not set", grid_idx);
+    CUDA_TRY(cudaSetDevice(g->device));
+    st = g->precision == 32 ? do_norm<float>(g, grid_idx, kind, out) : do_norm<double>(g, grid_idx, kind, out);
+    if (st != ROEAM_OK) return st;
+    return read_status(g);
+}
+
+roeam_status roeam_conserved_totals(roeam_grid *g, int grid_idx, double out[4])
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (grid_idx < 0) return fail(ROEAM_E_ARG, "conserved_totals needs one grid (grid_idx >= 0)");
+    if (!out) return fail(ROEAM_E_ARG, "out must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    st = g->precision == 32 ? do_totals<float>(g, grid_idx, out) : do_totals<double>(g, grid_idx, out);
+    if (st != ROEAM_OK) return st;
+    return read_status(g);
+}
+
+roeam_status roeam_check(roeam_grid *g)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    CUDA_TRY(cudaSetDevice(g->device));
+    return read_status(g);
+}
+
+unsigned long long roeam_launch_count(const roeam_grid *g) { return g ? g->launches : 0ull; }
+
+long long roeam_cell_count(const roeam_grid *g, int grid_idx)
+{
+    if (!g || grid_idx < -1 || grid_idx >= g->count) return -1;
+    if (grid_idx >= 0) return (long long)g->hg[grid_idx].ni * g->hg[grid_idx].nj;
+    return g->total_packed / 4;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// roeam_internal.h — device-side descriptors and launch entry points shared by the
+// library's host code (roeam_api.cu) and its kernel translation units (roeam_k32.cu,
+// roeam_k64.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace roeam {
+
+constexpr int BC_PERIODIC = 0, BC_WALL = 1, BC_INFLOW = 2, BC_OUTFLOW = 3;
+
+// Status bits raised by kernels (read back by the host at synchronising calls).
+constexpr unsigned ST_NONPOSITIVE = 1u, ST_NONFINITE = 2u;
+
+// Per-grid descriptor, resident in device memory, read-only in kernels.
+struct GridDev {
+    long long off;    // element offset of this grid's variable-0 plane in the state buffers
+    long long plane;  // elements per variable plane (nj * pitch)
+    long long voff;   // element offset of this grid's vertex displacement planes (-1: Cartesian)
+    long long soff;   // byte offset of this grid's solid mask (-1: none)
+    long long poff;   // element offset of this grid in the packed host layout [4][nj][ni]
+    int ni, nj, pitch, vpitch;
+    int ntx, nty, tile_base, ntiles;
+    int bc[4];        // W, E, S, N
+    int limiter;      // 1 minmod, 2 van Leer (MUSCL kernels)
+    int eps1, use_s1, xi_form;
+    double inflow[4]; // rho, u, v, p
+    double gamma, m_ref, u_ref, eps2;
+    double dx, dy;    // Cartesian spacings / reference-grid spacings of a curvilinear grid
+    double nfluid;    // number of fluid cells
+};
+
+enum Mode { MODE_STAGE = 0, MODE_RESIDUAL = 1, MODE_NORM = 2 };
+
+template <typename T>
+struct StageArgs {
+    const GridDev *grids;
+    const int *tile_base;   // ngrids + 1 prefix sums of tile counts
+    int ngrids;
+    int tile_lo, tile_hi;   // tiles [tile_lo, tile_hi) of the batch processed by this launch
+    const T *src;           // U^(k): the state whose residual is evaluated (halo source)
+    const T *un;            // U^n for the stage combination
+    T *dst;                 // stage output, or the residual in MODE_RESIDUAL
+    const T *vdx, *vdy;     // vertex displacement planes (curvilinear grids)
+    const uint8_t *solid;   // solid masks
+    T alpha, beta;          // dst = alpha * U^n + beta * (U^(k) + dt R(U^(k)))
+    int mode;
+    int want_rate;          // write each grid's max signal-speed rate of dst into rate_wr
+    const unsigned long long *rate_rd;  // per-grid max rate of U^n (double bits)
+    unsigned long long *rate_wr;        // per-grid max rate of the stage output (double bits)
+    unsigned long long *rate_zero;      // per-grid slots to reset (the next step's rate_wr), may be null
+    double cfl, dt_fixed;
+    unsigned *status;
+    double *partials;       // MODE_NORM: gridDim.x * 8 (sum R^2 [4], max |R| [4])
+};
+
+// Tile shapes the stage kernel is instantiated for (TX x TY cells, NT threads).
+struct TileCfg { int tx, ty, nt; };
+constexpr int NUM_TILE_CFGS = 3;
+constexpr TileCfg TILE_CFGS[NUM_TILE_CFGS] = {{32, 8, 256}, {32, 16, 512}, {64, 8, 512}};
+
+template <typename T>
+struct Launchers {
+    // Fused face-flux / residual / stage kernel over tiles [tile_lo, tile_hi).
+    static cudaError_t stage(const StageArgs<T> &a, int muscl, int curv, int cfg, int nblocks, cudaStream_t s);
+    // Largest resident CTAs per SM of a stage-kernel variant (for persistent launches).
+    static int stage_occupancy(int muscl, int curv, int cfg);
+    // Max signal-speed rate of a state into rate[g] (slot zeroed first by the caller).
+    static cudaError_t rate(const GridDev *grids, int g_lo, int g_hi, const T *U, const T *vdx, const T *vdy,
+                            const uint8_t *solid, unsigned long long *rate, int curv, cudaStream_t s);
+    // Packed float64 [4][nj][ni] per grid <-> pitched working-precision planes.
+    static cudaError_t pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
+                            cudaStream_t s);
+    static cudaError_t unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, double *packed,
+                              cudaStream_t s);
+    // FP64 block partials of sum V*U over the fluid cells of one grid (gridDim.x * 4 doubles).
+    static cudaError_t totals(const GridDev *grids, int g, const T *U, const T *vdx, const T *vdy,
+                              const uint8_t *solid, double *partials, int nblocks, int curv, cudaStream_t s);
+};
+
+// Fixed-order reduction of nblocks x 8 norm partials into out[8] (sum[4], max[4]).
+cudaError_t launch_reduce_partials(const double *partials, int nblocks, int width, double *out, cudaStream_t s);
+
+}  // namespace roeam

@@ -1,0 +1,7 @@
+// FP32 instantiations of the Roe-AM kernels (state and flux arithmetic in float,
+// reductions and positivity re-decisions in double).
+#include "roeam_kernels.cuh"
+
+namespace roeam {
+template struct Launchers<float>;
+}

@@ -1,0 +1,30 @@
+// FP64 instantiations of the Roe-AM kernels.
+#include "roeam_kernels.cuh"
+
+namespace roeam {
+template struct Launchers<double>;
+
+// Fixed-order reduction of nblocks rows of `width` partials (first half sums, second half
+// maxima when width == 8; all sums when width == 4) into out[width]. One warp per column.
+__global__ void reduce_partials_kernel(const double *partials, int nblocks, int width, double *out)
+{
+    const int k = blockIdx.x;
+    const bool is_max = width == 8 && k >= 4;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) {
+        const double x = partials[(size_t)b * width + k];
+        v = is_max ? fmax(v, x) : v + x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double x = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmax(v, x) : v + x;
+    }
+    if (threadIdx.x == 0) out[k] = v;
+}
+
+cudaError_t launch_reduce_partials(const double *partials, int nblocks, int width, double *out, cudaStream_t s)
+{
+    reduce_partials_kernel<<<width, 32, 0, s>>>(partials, nblocks, width, out);
+    return cudaGetLastError();
+}
+}  // namespace roeam

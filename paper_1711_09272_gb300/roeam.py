@@ -1,0 +1,258 @@
+"""ctypes binding of the libroeam C ABI (include/roeam.h).
+
+Argument marshalling only: every step of the Roe-AM path runs in the library's CUDA
+kernels. The module-level functions keep the C names; `Batch` is a small convenience
+wrapper that owns a handle. There is no CPU fallback: if the compiled library is
+missing or no GPU is present, the calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libroeam.so")
+
+ROEAM_OK, ROEAM_E_ARG, ROEAM_E_CUDA, ROEAM_E_OOM, ROEAM_E_NONPOSITIVE, ROEAM_E_NONFINITE, ROEAM_E_TIMEOUT, \
+    ROEAM_E_STATE = range(8)
+STATUS_NAMES = ["OK", "E_ARG", "E_CUDA", "E_OOM", "E_NONPOSITIVE", "E_NONFINITE", "E_TIMEOUT", "E_STATE"]
+ROEAM_NORM_L2, ROEAM_NORM_LINF = 0, 1
+
+# Entry points declared in include/roeam.h (checked by the tests).
+EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual",
+           "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
+           "roeam_cell_count", "roeam_last_error", "roeam_version"]
+
+
+class RoeamError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"roeam {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+class roeam_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("m_ref", C.c_double), ("u_ref", C.c_double), ("eps2", C.c_double),
+                ("eps1", C.c_int), ("use_s1", C.c_int), ("recon", C.c_int), ("xi_form", C.c_int),
+                ("precision", C.c_int), ("reserved_", C.c_int)]
+
+
+class roeam_grid_desc(C.Structure):
+    _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("bc", C.c_int * 4), ("inflow", C.c_double * 4),
+                ("xv", C.POINTER(C.c_double)), ("yv", C.POINTER(C.c_double)), ("dx", C.c_double),
+                ("dy", C.c_double), ("solid", C.POINTER(C.c_uint8)), ("p", roeam_params)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libroeam.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libroeam.so not found at {path}; build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    lib.roeam_create_grid.argtypes = [C.c_int, C.POINTER(roeam_grid_desc), C.c_int, vp, C.POINTER(vp)]
+    lib.roeam_destroy_grid.argtypes = [vp]
+    lib.roeam_destroy_grid.restype = None
+    lib.roeam_set_state.argtypes = [vp, C.c_int, vp]
+    lib.roeam_get_state.argtypes = [vp, C.c_int, vp]
+    lib.roeam_flux_residual.argtypes = [vp, C.c_int, vp]
+    lib.roeam_rk_step.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp]
+    lib.roeam_residual_norm.argtypes = [vp, C.c_int, C.c_int, dp]
+    lib.roeam_conserved_totals.argtypes = [vp, C.c_int, dp]
+    lib.roeam_check.argtypes = [vp]
+    lib.roeam_launch_count.argtypes = [vp]
+    lib.roeam_launch_count.restype = C.c_ulonglong
+    lib.roeam_cell_count.argtypes = [vp, C.c_int]
+    lib.roeam_cell_count.restype = C.c_longlong
+    lib.roeam_last_error.restype = C.c_char_p
+    lib.roeam_version.restype = C.c_int
+    for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
+                 "roeam_residual_norm", "roeam_conserved_totals", "roeam_check"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != ROEAM_OK:
+        raise RoeamError(st, _lib.roeam_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (host, possibly pinned)."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+# ----------------------------------------------------------------------------- C names
+def roeam_create_grid(descs: Sequence[roeam_grid_desc], device: int = 0, cuda_stream: int = 0) -> int:
+    lib = load_library()
+    arr = (roeam_grid_desc * len(descs))(*descs)
+    h = C.c_void_p()
+    _check(lib.roeam_create_grid(len(descs), arr, device, C.c_void_p(cuda_stream or None), C.byref(h)))
+    return h.value
+
+
+def roeam_destroy_grid(h: int) -> None:
+    load_library().roeam_destroy_grid(C.c_void_p(h))
+
+
+def roeam_set_state(h: int, grid_idx: int, cons) -> None:
+    _check(load_library().roeam_set_state(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(cons))))
+
+
+def roeam_get_state(h: int, grid_idx: int, out) -> None:
+    _check(load_library().roeam_get_state(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(out))))
+
+
+def roeam_flux_residual(h: int, grid_idx: int, out=None) -> None:
+    _check(load_library().roeam_flux_residual(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(out) if out is not None else None)))
+
+
+def roeam_rk_step(h: int, cfl: float, dt_fixed: float, nsteps: int, dt_last=None) -> None:
+    _check(load_library().roeam_rk_step(C.c_void_p(h), cfl, dt_fixed, nsteps,
+                                        C.c_void_p(_ptr(dt_last) if dt_last is not None else None)))
+
+
+def roeam_residual_norm(h: int, grid_idx: int, kind: int = ROEAM_NORM_L2) -> np.ndarray:
+    out = np.zeros(4)
+    _check(load_library().roeam_residual_norm(C.c_void_p(h), grid_idx, kind, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def roeam_conserved_totals(h: int, grid_idx: int) -> np.ndarray:
+    out = np.zeros(4)
+    _check(load_library().roeam_conserved_totals(C.c_void_p(h), grid_idx, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def roeam_check(h: int) -> None:
+    _check(load_library().roeam_check(C.c_void_p(h)))
+
+
+def roeam_launch_count(h: int) -> int:
+    return int(load_library().roeam_launch_count(C.c_void_p(h)))
+
+
+def roeam_cell_count(h: int, grid_idx: int = -1) -> int:
+    return int(load_library().roeam_cell_count(C.c_void_p(h), grid_idx))
+
+
+def roeam_version() -> int:
+    return int(load_library().roeam_version())
+
+
+# ----------------------------------------------------------------------------- convenience
+def make_desc(spec, precision: int = 64, keep: Optional[list] = None) -> roeam_grid_desc:
+    """Descriptor from any object with the fields of workloads.GridSpec. Arrays it points
+    to are appended to `keep` so they outlive the create call."""
+    keep = keep if keep is not None else []
+    d = roeam_grid_desc()
+    d.ni, d.nj = int(spec.ni), int(spec.nj)
+    d.bc[:] = [int(b) for b in spec.bc]
+    d.inflow[:] = [float(x) for x in spec.inflow]
+    if spec.xv is not None:
+        xv = np.ascontiguousarray(spec.xv, dtype=np.float64)
+        yv = np.ascontiguousarray(spec.yv, dtype=np.float64)
+        keep += [xv, yv]
+        d.xv = xv.ctypes.data_as(C.POINTER(C.c_double))
+        d.yv = yv.ctypes.data_as(C.POINTER(C.c_double))
+    d.dx, d.dy = float(spec.dx), float(spec.dy)
+    if spec.solid is not None:
+        s = np.ascontiguousarray(spec.solid, dtype=np.uint8)
+        keep.append(s)
+        d.solid = s.ctypes.data_as(C.POINTER(C.c_uint8))
+    p = spec.params
+    d.p = roeam_params(p.gamma, p.m_ref, p.u_ref, p.eps2, int(p.eps1), int(p.use_s1), int(p.recon),
+                       int(p.xi_form), int(precision), 0)
+    return d
+
+
+class Batch:
+    """Owns a libroeam handle for a list of grid specs (workloads.GridSpec-like)."""
+
+    def __init__(self, specs, precision: int = 64, device: int = 0, cuda_stream: int = 0):
+        if not isinstance(specs, (list, tuple)):
+            specs = [specs]
+        self.specs = list(specs)
+        keep: list = []
+        descs = [make_desc(s, precision, keep) for s in self.specs]
+        self.handle = roeam_create_grid(descs, device, cuda_stream)
+        self.precision = precision
+        self.sizes = [s.ni * s.nj for s in self.specs]
+        self.offsets = np.concatenate([[0], np.cumsum([4 * n for n in self.sizes])]).astype(np.int64)
+
+    def close(self):
+        if self.handle:
+            roeam_destroy_grid(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _shape(self, idx):
+        s = self.specs[idx]
+        return (4, s.nj, s.ni)
+
+    def set_state(self, U, grid_idx: int = 0):
+        if grid_idx < 0:
+            roeam_set_state(self.handle, -1, U)
+        else:
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            assert U.shape == self._shape(grid_idx), (U.shape, self._shape(grid_idx))
+            roeam_set_state(self.handle, grid_idx, U)
+
+    def set_states(self, Us):
+        packed = np.concatenate([np.ascontiguousarray(U, dtype=np.float64).ravel() for U in Us])
+        roeam_set_state(self.handle, -1, packed)
+
+    def get_state(self, grid_idx: int = 0) -> np.ndarray:
+        out = np.empty(self._shape(grid_idx))
+        roeam_get_state(self.handle, grid_idx, out)
+        return out
+
+    def get_states(self):
+        packed = np.empty(int(self.offsets[-1]))
+        roeam_get_state(self.handle, -1, packed)
+        return [packed[self.offsets[k]:self.offsets[k + 1]].reshape(self._shape(k)) for k in range(len(self.specs))]
+
+    def residual(self, grid_idx: int = 0) -> np.ndarray:
+        out = np.empty(self._shape(grid_idx))
+        roeam_flux_residual(self.handle, grid_idx, out)
+        return out
+
+    def step(self, cfl: float = 0.5, dt_fixed: float = 0.0, nsteps: int = 1, want_dt: bool = False):
+        dt = np.zeros(len(self.specs)) if want_dt else None
+        roeam_rk_step(self.handle, cfl, dt_fixed, nsteps, dt)
+        return dt
+
+    def residual_norm(self, grid_idx: int = 0, kind: int = ROEAM_NORM_L2) -> np.ndarray:
+        return roeam_residual_norm(self.handle, grid_idx, kind)
+
+    def totals(self, grid_idx: int = 0) -> np.ndarray:
+        return roeam_conserved_totals(self.handle, grid_idx)
+
+    def check(self):
+        roeam_check(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return roeam_launch_count(self.handle)

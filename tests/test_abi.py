@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports every entry point include/roeam.h declares
+(no compute calls: this runs without a GPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "roeam.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(roeam_[a-z_]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_header_symbols():
+    from paper_1711_09272_gb300 import build as b
+    path = b.build()
+    assert os.path.exists(path)
+    import ctypes
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert "roeam_create_grid" in names and "roeam_rk_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    import paper_1711_09272_gb300 as P
+    assert sorted(P.EXPORTS) == declared_functions()
+    lib = P.load_library()
+    assert P.roeam_version() >= 10000
+    assert lib.roeam_last_error() is not None
+
+
+def test_create_rejects_bad_arguments_without_gpu_work():
+    """Argument validation happens before any device call."""
+    import workloads as W
+    import paper_1711_09272_gb300 as P
+    spec = W.GridSpec(ni=3, nj=8)
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam_create_grid([P.make_desc(spec)])
+    assert e.value.status == 1 and "ni, nj" in str(e.value)
+    spec = W.GridSpec(ni=8, nj=8, bc=(W.PERIODIC, W.WALL, W.PERIODIC, W.PERIODIC))
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam_create_grid([P.make_desc(spec)])
+    assert "PERIODIC" in str(e.value)
+    spec = W.with_params(W.GridSpec(ni=8, nj=8), gamma=1.0)
+    with pytest.raises(P.RoeamError):
+        P.roeam_create_grid([P.make_desc(spec)])
+    a = P.make_desc(W.GridSpec(ni=8, nj=8), precision=32)
+    b = P.make_desc(W.GridSpec(ni=8, nj=8), precision=64)
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam_create_grid([a, b])
+    assert "precision" in str(e.value)

@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (per-step state error, relative to max |U| per variable, as the error
+definition of the scheme's precision requirement states): FP64 <= 1e-12, FP32 <= 1e-5.
+Residuals are compared against the flux scale sum_f |F||S| / V, which bounds the
+rounding of their cancellation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 1e-5}
+
+
+def P():
+    import paper_1711_09272_gb300 as pkg
+    return pkg
+
+
+def rel_state_err(Ug, Uo):
+    return float(np.max(np.abs(Ug - Uo).reshape(4, -1).max(axis=1) / np.abs(Uo).reshape(4, -1).max(axis=1)))
+
+
+def one_step_parity(spec, U, prec, cfl=0.5, dt_fixed=0.0, **variant):
+    """Sets U on the GPU, reads back the (rounded) device state, advances one step on both
+    sides from that same state and returns the relative state error."""
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        U0 = b.get_state(0)
+        b.step(cfl=cfl, dt_fixed=dt_fixed, nsteps=1)
+        Ug = b.get_state(0)
+    Uo, _ = oracle.OracleGrid(spec, **variant).step(U0, cfl=cfl, dt_fixed=dt_fixed)
+    return rel_state_err(Ug, Uo)
+
+
+CASES = {
+    "periodic_first": lambda: (W.GridSpec(ni=77, nj=45, dx=0.013, dy=0.021, params=W.SchemeParams(m_ref=0.3)), 1.2),
+    "periodic_minmod": lambda: (W.GridSpec(ni=70, nj=37, dx=0.013, dy=0.021,
+                                           params=W.SchemeParams(m_ref=0.3, recon=1)), 1.2),
+    "periodic_vanleer_eps1": lambda: (W.GridSpec(ni=66, nj=41, dx=0.02, dy=0.02,
+                                                 params=W.SchemeParams(m_ref=0.8, recon=2, eps1=1)), 2.5),
+    "no_detector_xi_literal": lambda: (W.GridSpec(ni=40, nj=33, params=W.SchemeParams(use_s1=0, xi_form=1)), 1.5),
+    "low_mach": lambda: (W.GridSpec(ni=48, nj=40, params=W.SchemeParams(m_ref=1e-3, recon=1)), 0.01),
+}
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_step_parity_rough_states(case, prec):
+    spec, mach = CASES[case]()
+    U = W.random_rough_state(spec, seed=101, mach=mach, jump=0.4)
+    err = one_step_parity(spec, U, prec)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_step_parity_walls_inflow_outflow(prec):
+    spec, U = W.quirk(nx=90, ny=20, eps_y=0.1, x_shock=30.0, eps1=1, recon=2)
+    U = U + 0.02 * W.random_smooth_state(spec, seed=5, mach=0.3, amp=0.3) * np.array([1, 0, 0, 1])[:, None, None]
+    assert one_step_parity(spec, U, prec, cfl=0.4) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("recon", [0, 2])
+def test_step_parity_warped_periodic(prec, recon):
+    spec = W.with_params(W.warped_periodic(40, amp=0.2), recon=recon, m_ref=0.4)
+    U = W.random_smooth_state(spec, seed=11, mach=0.7, amp=0.5)
+    assert one_step_parity(spec, U, prec) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_step_parity_step_with_solid_block(prec):
+    spec, U = W.warped_step(120, 40, recon=2)
+    U = U * (1 + 0.05 * W.random_smooth_state(spec, seed=3, mach=0.3, amp=0.5)[0:1])
+    assert one_step_parity(spec, U, prec, cfl=0.4) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_residual_parity(prec):
+    spec = W.GridSpec(ni=53, nj=29, dx=0.05, dy=0.04, params=W.SchemeParams(m_ref=0.5, recon=2, eps1=1))
+    U = W.random_rough_state(spec, seed=7, mach=1.5, jump=0.5)
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        U0 = b.get_state(0)
+        Rg = b.residual(0)
+    g = oracle.OracleGrid(spec)
+    Ro = g.residual(U0)
+    rho, u, v, p = W.cons_to_prim(U0)
+    fscale = np.max(rho * (np.abs(u) + np.abs(v)) ** 2 + p + (p * 3.5 + rho * (u * u + v * v)) * (np.abs(u) + np.abs(v) + 2))
+    scale = fscale * 4 / min(spec.dx, spec.dy)
+    err = np.max(np.abs(Rg - Ro)) / scale
+    assert err <= (1e-13 if prec == 64 else 2e-6), err
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_free_stream_exact(prec):
+    spec = W.GridSpec(ni=70, nj=19, dx=0.1, dy=0.1, params=W.SchemeParams(recon=2, m_ref=0.1))
+    U = W.free_stream(spec, 1.3, 0.2, -0.1, 0.8)
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        assert np.all(b.residual(0) == 0.0)
+        U0 = b.get_state(0)
+        b.step(0.5, nsteps=3)
+        # the stage combinations 3/4 U + 1/4 U and 1/3 U + 2/3 U round to within a few ulp
+        assert rel_state_err(b.get_state(0), U0) <= 8 * np.finfo(np.float32 if prec == 32 else np.float64).eps
+
+
+def test_multi_step_vortex_trajectory_fp64():
+    """Config-1 workload (64x64 periodic isentropic vortex, first order, CFL 0.5, 100 steps):
+    the FP64 GPU trajectory stays with the oracle's."""
+    spec, U = W.isentropic_vortex(64)
+    with P().Batch([spec], precision=64) as b:
+        b.set_state(U, 0)
+        b.step(0.5, nsteps=100)
+        Ug = b.get_state(0)
+    Uo, _ = oracle.OracleGrid(spec).step(U, 0.5, nsteps=100)
+    assert rel_state_err(Ug, Uo) <= 1e-11
+
+
+def test_batch_ragged_grids_per_grid_dt():
+    specs, states = W.batch(count=7, seed=77, ni_range=(4, 90), nj_range=(4, 70))
+    with P().Batch(specs, precision=64) as b:
+        b.set_states(states)
+        dts = b.step(0.5, nsteps=1, want_dt=True)
+        got = b.get_states()
+    for k, (s, U) in enumerate(zip(specs, states)):
+        Uo, dto = oracle.OracleGrid(s).step(U, 0.5)
+        assert abs(dts[k] / dto - 1) < 1e-12
+        assert rel_state_err(got[k], Uo) <= 1e-12, k
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_graph_replay_matches_direct_steps(prec):
+    spec = W.GridSpec(ni=50, nj=30, params=W.SchemeParams(recon=1))
+    U = W.random_smooth_state(spec, seed=2, mach=0.6, amp=0.3)
+    with P().Batch([spec], precision=prec) as b1, P().Batch([spec], precision=prec) as b2:
+        b1.set_state(U, 0)
+        b2.set_state(U, 0)
+        b1.step(0.5, nsteps=19)          # odd start, graph replays, direct tail
+        for _ in range(19):
+            b2.step(0.5, nsteps=1)
+        assert np.array_equal(b1.get_state(0), b2.get_state(0))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_totals_and_norms(prec):
+    spec = W.with_params(W.warped_periodic(32), recon=2)
+    U = W.random_smooth_state(spec, seed=4, mach=0.8, amp=0.4)
+    g = oracle.OracleGrid(spec)
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        U0 = b.get_state(0)
+        T0 = b.totals(0)
+        n2 = b.residual_norm(0, 0)
+        ninf = b.residual_norm(0, 1)
+        b.step(0.5, nsteps=10)
+        T1 = b.totals(0)
+    To = g.totals(U0)
+    assert np.all(np.abs(T0 - To) <= (1e-13 if prec == 64 else 1e-6) * np.abs(To).max())
+    assert np.all(np.abs(T1 - T0) <= (1e-13 if prec == 64 else 1e-5) * np.abs(T0).max())
+    R = g.residual(U0)
+    assert np.allclose(n2, np.sqrt(np.mean(R.reshape(4, -1) ** 2, axis=1)), rtol=1e-10 if prec == 64 else 1e-3,
+                       atol=1e-12 * np.abs(R).max())
+    assert np.allclose(ninf, np.abs(R).reshape(4, -1).max(axis=1), rtol=1e-10 if prec == 64 else 1e-3,
+                       atol=1e-12 * np.abs(R).max())
+
+
+def test_nonpositive_state_is_reported():
+    """A host-made invalid state (negative pressure) is reported as a status, not a fault."""
+    spec = W.GridSpec(ni=16, nj=16)
+    U = W.free_stream(spec)
+    U[3, 5, 5] = 0.01 * U[3, 5, 5] - 10.0
+    import paper_1711_09272_gb300 as pkg
+    with pkg.Batch([spec], precision=64) as b:
+        b.set_state(U, 0)
+        b.step(cfl=0.5, dt_fixed=1e-3, nsteps=1)
+        with pytest.raises(pkg.RoeamError) as e:
+            b.check()
+        assert e.value.status in (4, 5)
+        b.check()   # the status was cleared
