@@ -136,6 +136,22 @@ roeam_status roeam_conserved_totals(roeam_grid *g, int grid_idx, double out[4]);
  * (ROEAM_E_NONPOSITIVE / ROEAM_E_NONFINITE), clearing it; ROEAM_OK if none. */
 roeam_status roeam_check(roeam_grid *g);
 
+/* Number of tile shapes (stage-kernel variants) the library is built with. */
+int roeam_tile_config_count(void);
+
+/* Describes tile shape `cfg`: tile width tx, height ty (cells) and threads per CTA. */
+roeam_status roeam_tile_config_info(int cfg, int *tx, int *ty, int *threads);
+
+/* Selects tile shape `cfg` for this handle's stage kernels (default 0). Captured graphs
+ * are rebuilt on the next step. */
+roeam_status roeam_set_tile_config(roeam_grid *g, int cfg);
+
+/* Autotuner: times `steps` SSP-RK3 steps at `cfl` with every tile shape on the current
+ * state, restores the state after each trial, and keeps the fastest shape. best_cfg
+ * (nullable) receives it; ms_per_step (nullable, roeam_tile_config_count() doubles) the
+ * measured time per step of each shape. Synchronises; allocates a temporary copy of the state. */
+roeam_status roeam_autotune(roeam_grid *g, double cfl, int steps, int *best_cfg, double *ms_per_step);
+
 /* Number of kernels this handle has launched (graph nodes count one each per replay). */
 unsigned long long roeam_launch_count(const roeam_grid *g);
 

@@ -57,7 +57,7 @@ struct roeam_grid {
     int device = 0;
     cudaStream_t stream = nullptr;       // user stream (work is ordered on it)
     cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
-    int precision = 32, muscl = 0, curv = 0, count = 0;
+    int precision = 32, muscl = 0, curv = 0, walls = 0, count = 0;
     size_t esize = 4;
     int tile_cfg = 0;
     int nblocks = 0;        // persistent CTAs of the stage kernel
@@ -69,7 +69,10 @@ struct roeam_grid {
     std::vector<int> h_tile_base;
     std::vector<char> state_set;
     GridDev *d_grids = nullptr;
-    int *d_tile_base = nullptr;
+    void *d_coef = nullptr;                              // GridCoef<T>[count]
+    int4 *d_units_grid = nullptr;   // work units grouped by grid (per-grid launches)
+    int4 *d_units_all = nullptr;    // the same units ordered by decreasing size (whole-batch launches)
+    int units_cap = 0;
     void *U = nullptr, *A = nullptr, *B = nullptr;      // U^n (in place), stage buffers
     void *vdx = nullptr, *vdy = nullptr;
     uint8_t *solid = nullptr;
@@ -89,29 +92,50 @@ struct roeam_grid {
 
 namespace {
 
+// Work units of the stage kernel for shape `cfg`: every grid is cut into strips of
+// 32 - 2H interior columns and into ceil(nj / ty) segments of nearly equal height. Units are
+// stored grouped by grid (for launches over one grid) and, for whole-batch launches, ordered
+// by decreasing height so that the static round-robin over warps stays balanced.
 roeam_status setup_tiles(roeam_grid *g, int cfg)
 {
     const TileCfg tc = TILE_CFGS[cfg];
     g->tile_cfg = cfg;
+    const int H = g->muscl ? 2 : 1;
+    const int width = tc.tx - 2 * H;
+    std::vector<int4> ug;
     g->h_tile_base.assign(g->count + 1, 0);
-    int base = 0;
     for (int k = 0; k < g->count; ++k) {
         GridDev &G = g->hg[k];
-        G.ntx = (G.ni + tc.tx - 1) / tc.tx;
+        G.ntx = (G.ni + width - 1) / width;
         G.nty = (G.nj + tc.ty - 1) / tc.ty;
         G.ntiles = G.ntx * G.nty;
-        G.tile_base = base;
-        g->h_tile_base[k] = base;
-        base += G.ntiles;
+        G.tile_base = (int)ug.size();
+        g->h_tile_base[k] = G.tile_base;
+        for (int sg = 0; sg < G.nty; ++sg) {
+            const int j0 = (int)((long long)sg * G.nj / G.nty), j1 = (int)((long long)(sg + 1) * G.nj / G.nty);
+            for (int st = 0; st < G.ntx; ++st) ug.push_back(make_int4(k, st * width - H, j0, j1));
+        }
     }
+    const int base = (int)ug.size();
     g->h_tile_base[g->count] = base;
     g->total_tiles = base;
+    std::vector<int4> ua(ug);
+    std::stable_sort(ua.begin(), ua.end(), [](const int4 &a, const int4 &b) { return (a.w - a.z) > (b.w - b.z); });
+    if (base > g->units_cap) {
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        cudaFree(g->d_units_grid);
+        cudaFree(g->d_units_all);
+        g->d_units_grid = g->d_units_all = nullptr;
+        CUDA_TRY(cudaMalloc(&g->d_units_grid, sizeof(int4) * base));
+        CUDA_TRY(cudaMalloc(&g->d_units_all, sizeof(int4) * base));
+        g->units_cap = base;
+    }
     CUDA_TRY(cudaMemcpyAsync(g->d_grids, g->hg.data(), sizeof(GridDev) * g->count, cudaMemcpyHostToDevice, g->stream));
-    CUDA_TRY(cudaMemcpyAsync(g->d_tile_base, g->h_tile_base.data(), sizeof(int) * (g->count + 1),
-                             cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->d_units_grid, ug.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->d_units_all, ua.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    const int occ = g->precision == 32 ? Launchers<float>::stage_occupancy(g->muscl, g->curv, cfg)
-                                       : Launchers<double>::stage_occupancy(g->muscl, g->curv, cfg);
+    const int occ = g->precision == 32 ? Launchers<float>::stage_occupancy(g->muscl, g->curv, g->walls)
+                                       : Launchers<double>::stage_occupancy(g->muscl, g->curv, g->walls);
     g->nblocks = std::max(1, occ * g->num_sms);
     for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
     g->graphs.clear();
@@ -138,6 +162,31 @@ roeam_status upload_geometry(roeam_grid *g, const roeam_grid_desc *d)
     return ROEAM_OK;
 }
 
+template <typename T>
+roeam_status upload_coef(roeam_grid *g)
+{
+    std::vector<GridCoef<T>> h(g->count);
+    for (int k = 0; k < g->count; ++k) {
+        const GridDev &G = g->hg[k];
+        GridCoef<T> &c = h[k];
+        c.g = T(G.gamma);
+        c.gm1 = T(G.gamma - 1.0);
+        c.gm1i = T(1.0 / (G.gamma - 1.0));
+        c.hgm1 = T(0.5 * (G.gamma - 1.0));
+        c.mr2 = T(G.m_ref * G.m_ref);
+        c.rr_thr = T(1e-5 * G.u_ref);
+        c.eps2 = T(G.eps2);
+        c.dx = T(G.dx);
+        c.dy = T(G.dy);
+        c.V = T(G.dx * G.dy);
+        c.Vi = T(1.0 / (G.dx * G.dy));
+        for (int s = 0; s < 4; ++s) c.inflow[s] = T(G.inflow[s]);
+    }
+    CUDA_TRY(cudaMalloc(&g->d_coef, sizeof(GridCoef<T>) * g->count));
+    CUDA_TRY(cudaMemcpy(g->d_coef, h.data(), sizeof(GridCoef<T>) * g->count, cudaMemcpyHostToDevice));
+    return ROEAM_OK;
+}
+
 // Stage-kernel arguments common to every mode.
 template <typename T>
 StageArgs<T> base_args(roeam_grid *g)
@@ -145,7 +194,8 @@ StageArgs<T> base_args(roeam_grid *g)
     StageArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.grids = g->d_grids;
-    a.tile_base = g->d_tile_base;
+    a.coef = (const GridCoef<T> *)g->d_coef;
+    a.units = g->d_units_all;
     a.ngrids = g->count;
     a.tile_lo = 0;
     a.tile_hi = g->total_tiles;
@@ -168,15 +218,17 @@ roeam_status launch_step(roeam_grid *g, cudaStream_t s, long long step, double c
     a.rate_rd = rd;
     a.cfl = cfl;
     a.dt_fixed = dt_fixed;
+    a.cfl_t = T(cfl);
+    a.dt_fixed_t = T(dt_fixed);
     // Stage 1: U1 = U^n + dt R(U^n)
     a.src = U; a.un = U; a.dst = A; a.alpha = T(0); a.beta = T(1); a.rate_zero = wr; a.want_rate = 0;
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, s));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, s));
     // Stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt R(U1))
     a.src = A; a.un = U; a.dst = B; a.alpha = T(0.75); a.beta = T(0.25); a.rate_zero = nullptr;
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, s));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, s));
     // Stage 3: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt R(U2)), in place; rate of U^{n+1} for the next dt
     a.src = B; a.un = U; a.dst = U; a.alpha = T(1.0 / 3.0); a.beta = T(2.0 / 3.0); a.rate_wr = wr; a.want_rate = 1;
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, s));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, s));
     return ROEAM_OK;
 }
 
@@ -185,8 +237,8 @@ roeam_status refresh_rate(roeam_grid *g, int lo, int hi)
 {
     unsigned long long *slot = g->rate + (size_t)(g->step & 1) * g->count;
     CUDA_TRY(cudaMemsetAsync(slot + lo, 0, sizeof(unsigned long long) * (hi - lo), g->stream));
-    CUDA_TRY(Launchers<T>::rate(g->d_grids, lo, hi, (const T *)g->U, (const T *)g->vdx, (const T *)g->vdy, g->solid,
-                                slot, g->curv, g->stream));
+    CUDA_TRY(Launchers<T>::rate(g->d_grids, (const GridCoef<T> *)g->d_coef, lo, hi, (const T *)g->U,
+                                (const T *)g->vdx, (const T *)g->vdy, g->solid, slot, g->curv, g->stream));
     g->launches += 1;
     return ROEAM_OK;
 }
@@ -299,8 +351,8 @@ roeam_status do_residual(roeam_grid *g, int idx, double *out)
     a.src = (const T *)g->U;
     a.un = (const T *)g->U;
     a.dst = (T *)g->A;
-    if (idx >= 0) { a.tile_lo = g->h_tile_base[idx]; a.tile_hi = g->h_tile_base[idx + 1]; }
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, g->nblocks, g->stream));
+    if (idx >= 0) { a.units = g->d_units_grid; a.tile_lo = g->h_tile_base[idx]; a.tile_hi = g->h_tile_base[idx + 1]; }
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, g->stream));
     g->launches += 1;
     if (out) return do_get<T>(g, idx, g->A, out);
     return ROEAM_OK;
@@ -313,12 +365,13 @@ roeam_status do_norm(roeam_grid *g, int idx, int kind, double out[4])
     a.mode = MODE_NORM;
     a.src = (const T *)g->U;
     a.un = (const T *)g->U;
+    a.units = g->d_units_grid;
     a.tile_lo = g->h_tile_base[idx];
     a.tile_hi = g->h_tile_base[idx + 1];
     a.partials = g->partials;
     const int nb = std::min(g->nblocks, std::min(g->partial_rows, a.tile_hi - a.tile_lo));
     CUDA_TRY(cudaMemsetAsync(g->partials, 0, sizeof(double) * 8 * g->partial_rows, g->stream));
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->tile_cfg, nb, g->stream));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, nb, g->stream));
     CUDA_TRY(launch_reduce_partials(g->partials, nb, 8, g->red_out, g->stream));
     g->launches += 2;
     CUDA_TRY(cudaMemcpyAsync(g->h_red, g->red_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, g->stream));
@@ -333,8 +386,8 @@ roeam_status do_totals(roeam_grid *g, int idx, double out[4])
 {
     const long long n = (long long)g->hg[idx].ni * g->hg[idx].nj;
     const int nb = (int)std::min<long long>(std::min<long long>((n + 255) / 256, 2 * g->partial_rows), 1024);
-    CUDA_TRY(Launchers<T>::totals(g->d_grids, idx, (const T *)g->U, (const T *)g->vdx, (const T *)g->vdy, g->solid,
-                                  g->partials, nb, g->curv, g->stream));
+    CUDA_TRY(Launchers<T>::totals(g->d_grids, (const GridCoef<T> *)g->d_coef, idx, (const T *)g->U,
+                                  (const T *)g->vdx, (const T *)g->vdy, g->solid, g->partials, nb, g->curv, g->stream));
     CUDA_TRY(launch_reduce_partials(g->partials, nb, 4, g->red_out, g->stream));
     g->launches += 2;
     CUDA_TRY(cudaMemcpyAsync(g->h_red, g->red_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, g->stream));
@@ -445,6 +498,9 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
         poff += 4ll * q.ni * q.nj;
         g->max_cells = std::max(g->max_cells, q.ni * q.nj);
         for (int s = 0; s < 4; ++s) G.bc[s] = q.bc[s];
+        for (int s = 0; s < 4; ++s)
+            if (q.bc[s] == ROEAM_BC_WALL) g->walls = 1;
+        if (q.solid) g->walls = 1;
         for (int s = 0; s < 4; ++s) G.inflow[s] = q.inflow[s];
         G.limiter = q.p.recon;
         G.eps1 = q.p.eps1;
@@ -474,7 +530,6 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
     CREATE_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     CREATE_TRY(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));
     CREATE_TRY(cudaMalloc(&g->d_grids, sizeof(GridDev) * count));
-    CREATE_TRY(cudaMalloc(&g->d_tile_base, sizeof(int) * (count + 1)));
     const size_t sbytes = g->esize * (size_t)g->total_elems;
     CREATE_TRY(cudaMalloc(&g->U, sbytes));
     CREATE_TRY(cudaMalloc(&g->A, sbytes));
@@ -507,6 +562,8 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
     CREATE_TRY(cudaMallocHost(&g->h_rate, sizeof(unsigned long long) * count));
     st = g->precision == 32 ? upload_geometry<float>(g, descs) : upload_geometry<double>(g, descs);
     if (st != ROEAM_OK) return cleanup(st);
+    st = g->precision == 32 ? upload_coef<float>(g) : upload_coef<double>(g);
+    if (st != ROEAM_OK) return cleanup(st);
     st = setup_tiles(g, 0);
     if (st != ROEAM_OK) return cleanup(st);
 #undef CREATE_TRY
@@ -521,7 +578,9 @@ void roeam_destroy_grid(roeam_grid *g)
     if (g->stream) cudaStreamSynchronize(g->stream); else cudaDeviceSynchronize();
     for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
     cudaFree(g->d_grids);
-    cudaFree(g->d_tile_base);
+    cudaFree(g->d_coef);
+    cudaFree(g->d_units_grid);
+    cudaFree(g->d_units_all);
     cudaFree(g->U);
     cudaFree(g->A);
     cudaFree(g->B);
@@ -593,8 +652,15 @@ roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nstep
             CUDA_TRY(cudaStreamSynchronize(g->stream));
             for (int k = 0; k < g->count; ++k) {
                 double r;
-                std::memcpy(&r, g->h_rate + k, sizeof(double));
-                dt_last[k] = cfl / r;
+                if (g->precision == 32) {
+                    float f;
+                    const uint32_t lo = (uint32_t)(g->h_rate[k] & 0xffffffffull);
+                    std::memcpy(&f, &lo, sizeof(float));
+                    dt_last[k] = (double)(float(cfl) / f);
+                } else {
+                    std::memcpy(&r, g->h_rate + k, sizeof(double));
+                    dt_last[k] = cfl / r;
+                }
             }
         }
         return read_status(g);
@@ -632,6 +698,78 @@ roeam_status roeam_check(roeam_grid *g)
 {
     if (!g) return fail(ROEAM_E_ARG, "null handle");
     CUDA_TRY(cudaSetDevice(g->device));
+    return read_status(g);
+}
+
+int roeam_tile_config_count(void) { return NUM_TILE_CFGS; }
+
+roeam_status roeam_tile_config_info(int cfg, int *tx, int *ty, int *threads)
+{
+    if (cfg < 0 || cfg >= NUM_TILE_CFGS) return fail(ROEAM_E_ARG, "tile config %d out of range", cfg);
+    if (tx) *tx = TILE_CFGS[cfg].tx;
+    if (ty) *ty = TILE_CFGS[cfg].ty;
+    if (threads) *threads = TILE_CFGS[cfg].nt;
+    return ROEAM_OK;
+}
+
+roeam_status roeam_set_tile_config(roeam_grid *g, int cfg)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    if (cfg < 0 || cfg >= NUM_TILE_CFGS) return fail(ROEAM_E_ARG, "tile config %d out of range", cfg);
+    CUDA_TRY(cudaSetDevice(g->device));
+    return setup_tiles(g, cfg);
+}
+
+roeam_status roeam_autotune(roeam_grid *g, double cfl, int steps, int *best_cfg, double *ms_per_step)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    if (steps < 1 || !(cfl > 0.0)) return fail(ROEAM_E_ARG, "need steps >= 1 and cfl > 0");
+    for (int k = 0; k < g->count; ++k)
+        if (!g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
+    CUDA_TRY(cudaSetDevice(g->device));
+    const size_t sbytes = g->esize * (size_t)g->total_elems;
+    const size_t rbytes = sizeof(unsigned long long) * 2 * g->count;
+    void *save = nullptr;
+    CUDA_TRY(cudaMalloc(&save, sbytes + rbytes));
+    const long long step0 = g->step;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    roeam_status st = ROEAM_OK;
+    int best = g->tile_cfg;
+    double best_ms = 1e300;
+    auto run = [&]() -> roeam_status {
+        if (cudaMemcpyAsync(save, g->U, sbytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess ||
+            cudaMemcpyAsync((char *)save + sbytes, g->rate, rbytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess ||
+            cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            return fail(ROEAM_E_CUDA, "autotune setup failed");
+        for (int cfg = 0; cfg < NUM_TILE_CFGS; ++cfg) {
+            roeam_status s2 = setup_tiles(g, cfg);
+            if (s2 != ROEAM_OK) return s2;
+            s2 = g->precision == 32 ? rk_steps<float>(g, cfl, 0.0, 1) : rk_steps<double>(g, cfl, 0.0, 1);   // warm-up
+            if (s2 != ROEAM_OK) return s2;
+            CUDA_TRY(cudaEventRecord(e0, g->stream));
+            s2 = g->precision == 32 ? rk_steps<float>(g, cfl, 0.0, steps) : rk_steps<double>(g, cfl, 0.0, steps);
+            if (s2 != ROEAM_OK) return s2;
+            CUDA_TRY(cudaEventRecord(e1, g->stream));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            const double per = ms / steps;
+            if (ms_per_step) ms_per_step[cfg] = per;
+            if (per < best_ms) { best_ms = per; best = cfg; }
+            // restore the state, the rate slots and the step parity
+            CUDA_TRY(cudaMemcpyAsync(g->U, save, sbytes, cudaMemcpyDeviceToDevice, g->stream));
+            CUDA_TRY(cudaMemcpyAsync(g->rate, (char *)save + sbytes, rbytes, cudaMemcpyDeviceToDevice, g->stream));
+            g->step = step0;
+        }
+        return setup_tiles(g, best);
+    };
+    st = run();
+    cudaStreamSynchronize(g->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (st != ROEAM_OK) return st;
+    if (best_cfg) *best_cfg = best;
     return read_status(g);
 }
 

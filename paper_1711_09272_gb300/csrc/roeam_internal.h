@@ -33,12 +33,22 @@ struct GridDev {
 
 enum Mode { MODE_STAGE = 0, MODE_RESIDUAL = 1, MODE_NORM = 2 };
 
+// Per-grid constants in the working precision, computed once on the host so that the
+// FP32 kernels execute no FP64 arithmetic on their hot path.
+template <typename T>
+struct GridCoef {
+    T g, gm1, gm1i, hgm1, mr2, rr_thr, eps2;   // gamma, gamma-1, 1/(gamma-1), (gamma-1)/2, M_ref^2, 1e-5 U_ref, eps2
+    T dx, dy, V, Vi;                     // spacings (reference spacings if curvilinear), dx*dy, 1/(dx*dy)
+    T inflow[4];                         // rho, u, v, p of INFLOW sides
+};
+
 template <typename T>
 struct StageArgs {
     const GridDev *grids;
-    const int *tile_base;   // ngrids + 1 prefix sums of tile counts
+    const GridCoef<T> *coef;
+    const int4 *units;      // work units: (grid, column of lane 0, first row, end row)
     int ngrids;
-    int tile_lo, tile_hi;   // tiles [tile_lo, tile_hi) of the batch processed by this launch
+    int tile_lo, tile_hi;   // work units [tile_lo, tile_hi) of the batch processed by this launch
     const T *src;           // U^(k): the state whose residual is evaluated (halo source)
     const T *un;            // U^n for the stage combination
     T *dst;                 // stage output, or the residual in MODE_RESIDUAL
@@ -47,36 +57,46 @@ struct StageArgs {
     T alpha, beta;          // dst = alpha * U^n + beta * (U^(k) + dt R(U^(k)))
     int mode;
     int want_rate;          // write each grid's max signal-speed rate of dst into rate_wr
-    const unsigned long long *rate_rd;  // per-grid max rate of U^n (double bits)
-    unsigned long long *rate_wr;        // per-grid max rate of the stage output (double bits)
+    const unsigned long long *rate_rd;  // per-grid max rate of U^n (working-precision bits)
+    unsigned long long *rate_wr;        // per-grid max rate of the stage output
     unsigned long long *rate_zero;      // per-grid slots to reset (the next step's rate_wr), may be null
     double cfl, dt_fixed;
+    T cfl_t, dt_fixed_t;    // the same in the working precision
     unsigned *status;
     double *partials;       // MODE_NORM: gridDim.x * 8 (sum R^2 [4], max |R| [4])
 };
 
-// Tile shapes the stage kernel is instantiated for (TX x TY cells, NT threads).
+// Work-unit shapes of the stage kernel: a warp sweeps a strip tx = 32 lanes wide (2H of
+// them halo) over ty rows; nt threads per CTA. The autotuner picks among these.
+constexpr int STAGE_THREADS = 128;
+#ifndef STAGE_MIN_BLOCKS
+#define STAGE_MIN_BLOCKS 3
+#endif
 struct TileCfg { int tx, ty, nt; };
-constexpr int NUM_TILE_CFGS = 3;
-constexpr TileCfg TILE_CFGS[NUM_TILE_CFGS] = {{32, 8, 256}, {32, 16, 512}, {64, 8, 512}};
+constexpr int NUM_TILE_CFGS = 4;
+constexpr TileCfg TILE_CFGS[NUM_TILE_CFGS] = {{32, 32, STAGE_THREADS}, {32, 64, STAGE_THREADS},
+                                              {32, 16, STAGE_THREADS}, {32, 128, STAGE_THREADS}};
 
 template <typename T>
 struct Launchers {
     // Fused face-flux / residual / stage kernel over tiles [tile_lo, tile_hi).
-    static cudaError_t stage(const StageArgs<T> &a, int muscl, int curv, int cfg, int nblocks, cudaStream_t s);
+    // walls: some grid of the batch has a WALL side or solid cells.
+    static cudaError_t stage(const StageArgs<T> &a, int muscl, int curv, int walls, int nblocks, cudaStream_t s);
     // Largest resident CTAs per SM of a stage-kernel variant (for persistent launches).
-    static int stage_occupancy(int muscl, int curv, int cfg);
+    static int stage_occupancy(int muscl, int curv, int walls);
     // Max signal-speed rate of a state into rate[g] (slot zeroed first by the caller).
-    static cudaError_t rate(const GridDev *grids, int g_lo, int g_hi, const T *U, const T *vdx, const T *vdy,
-                            const uint8_t *solid, unsigned long long *rate, int curv, cudaStream_t s);
+    static cudaError_t rate(const GridDev *grids, const GridCoef<T> *coef, int g_lo, int g_hi, const T *U,
+                            const T *vdx, const T *vdy, const uint8_t *solid, unsigned long long *rate, int curv,
+                            cudaStream_t s);
     // Packed float64 [4][nj][ni] per grid <-> pitched working-precision planes.
     static cudaError_t pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
                             cudaStream_t s);
     static cudaError_t unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, double *packed,
                               cudaStream_t s);
     // FP64 block partials of sum V*U over the fluid cells of one grid (gridDim.x * 4 doubles).
-    static cudaError_t totals(const GridDev *grids, int g, const T *U, const T *vdx, const T *vdy,
-                              const uint8_t *solid, double *partials, int nblocks, int curv, cudaStream_t s);
+    static cudaError_t totals(const GridDev *grids, const GridCoef<T> *coef, int g, const T *U, const T *vdx,
+                              const T *vdy, const uint8_t *solid, double *partials, int nblocks, int curv,
+                              cudaStream_t s);
 };
 
 // Fixed-order reduction of nblocks x 8 norm partials into out[8] (sum[4], max[4]).

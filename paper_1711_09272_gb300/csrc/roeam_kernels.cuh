@@ -1,17 +1,20 @@
 // roeam_kernels.cuh — sm_103a kernels of the Roe-AM finite-volume step.
 //
-// One fused kernel evaluates a whole Runge-Kutta stage per tile of TX x TY cells:
-//   1. halo load: the tile plus a 1-cell (first order) or 2-cell (MUSCL) halo is read
-//      once from HBM (structure-of-arrays planes, coalesced along i); ghost cells are
-//      generated on the fly from the boundary conditions (periodic wrap, wall mirror,
-//      inflow state, zero-gradient outflow), so no separate boundary kernel runs;
-//   2. the ratio indicator P of Eq. 97 on every face the tile's detectors need;
-//   3. the Roe-AM flux of Section 6.2 (Eqs. 85-109) on each x- and y-face of the tile,
-//      with the detector s1 of Eqs. 95-96, MUSCL reconstruction when enabled;
-//   4. the residual R = -(1/V) sum_f F_f |S_f| and the SSP-RK3 combination with U^n,
-//      plus the next step's time-step rate and the positivity/finiteness status.
-// The kernel is persistent: each CTA strides over the flattened tile list of every grid
-// of the batch, so ragged batches of uneven grids run in one launch.
+// The stage kernel evaluates a whole Runge-Kutta stage: face fluxes of Section 6.2
+// (Eqs. 85-109), the finite-volume residual, and the SSP-RK3 combination, in one pass
+// over the state. Its work unit is one warp sweeping a strip of 32 columns (H halo lanes
+// on each side, H = 1 at first order, 2 with MUSCL) over a segment of rows in +j:
+//   - each lane keeps a rolling window of H+2 rows of its column in registers and
+//     prefetches the next row while it computes the current one, so every cell state is
+//     read from HBM once per stage (plus halo lanes and H+1 warm-up rows per segment);
+//   - neighbour states, detector ratios and fluxes move between lanes with warp shuffles:
+//     no shared memory and no block barrier;
+//   - ghost cells come from the boundary conditions on the fly (periodic wrap, wall
+//     mirror, inflow state, zero-gradient outflow), so no separate boundary kernel runs;
+//   - the flux is evaluated in the face frame (normal velocity first), which makes the
+//     Cartesian x- and y-faces the same computation; in FP32 a lane evaluates its west
+//     x-face and its south y-face together as packed float2 arithmetic (FFMA2, FADD2,
+//     FMUL2 on sm_100-class GPUs).
 #pragma once
 
 #include <cstdint>
@@ -20,19 +23,90 @@
 
 namespace roeam {
 
-// ------------------------------------------------------------------ scalar helpers
-template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
-template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
-template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
-template <typename T> __device__ __forceinline__ T sgn(T a) { return T(int(a > T(0)) - int(a < T(0))); }
-template <typename T> __device__ __forceinline__ T pow8(T a) { T a2 = a * a, a4 = a2 * a2; return a4 * a4; }
+__device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
 
-// Eq. 98: f(phi) = min(phi sqrt(4 + (1 - phi^2)^2) / (1 + phi^2), 1); exactly 1 for phi >= 1.
-template <typename T> __device__ __forceinline__ T fmach(T phi)
+// ------------------------------------------------------------------ math on scalars and pairs
+// V is float, double, or V2 (two floats evaluated as one packed pair). Comparisons give a
+// mask (bool, or B2 for pairs); sel(mask, a, b) picks per component.
+struct V2 { float2 v; };
+struct B2 { bool x, y; };
+
+__device__ __forceinline__ V2 mk2(float a, float b) { V2 r; r.v = make_float2(a, b); return r; }
+__device__ __forceinline__ V2 operator+(V2 a, V2 b) { V2 r; r.v = __fadd2_rn(a.v, b.v); return r; }
+__device__ __forceinline__ V2 operator*(V2 a, V2 b) { V2 r; r.v = __fmul2_rn(a.v, b.v); return r; }
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) { V2 r; r.v = __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v); return r; }
+__device__ __forceinline__ V2 operator-(V2 a) { return mk2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ V2 vfma(V2 a, V2 b, V2 c) { V2 r; r.v = __ffma2_rn(a.v, b.v, c.v); return r; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename V> struct Sc;
+template <> struct Sc<float> { using S = float; using M = bool; };
+template <> struct Sc<double> { using S = double; using M = bool; };
+template <> struct Sc<V2> { using S = float; using M = B2; };
+
+template <typename V> __device__ __forceinline__ V splat(typename Sc<V>::S c) { return V(c); }
+template <> __device__ __forceinline__ V2 splat<V2>(float c) { return mk2(c, c); }
+
+template <typename T> __device__ __forceinline__ T vmin(T a, T b) { return a < b ? a : b; }
+template <typename T> __device__ __forceinline__ T vmax(T a, T b) { return a > b ? a : b; }
+__device__ __forceinline__ V2 vmin(V2 a, V2 b) { return mk2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y)); }
+__device__ __forceinline__ V2 vmax(V2 a, V2 b) { return mk2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double vabs(double a) { return fabs(a); }
+__device__ __forceinline__ V2 vabs(V2 a) { return mk2(fabsf(a.v.x), fabsf(a.v.y)); }
+
+template <typename T> __device__ __forceinline__ bool lt(T a, T b) { return a < b; }
+template <typename T> __device__ __forceinline__ bool gt(T a, T b) { return a > b; }
+template <typename T> __device__ __forceinline__ bool ge(T a, T b) { return a >= b; }
+template <typename T> __device__ __forceinline__ bool eq(T a, T b) { return a == b; }
+__device__ __forceinline__ B2 lt(V2 a, V2 b) { return {a.v.x < b.v.x, a.v.y < b.v.y}; }
+__device__ __forceinline__ B2 gt(V2 a, V2 b) { return {a.v.x > b.v.x, a.v.y > b.v.y}; }
+__device__ __forceinline__ B2 ge(V2 a, V2 b) { return {a.v.x >= b.v.x, a.v.y >= b.v.y}; }
+__device__ __forceinline__ B2 eq(V2 a, V2 b) { return {a.v.x == b.v.x, a.v.y == b.v.y}; }
+__device__ __forceinline__ B2 operator&&(B2 a, B2 b) { return {a.x && b.x, a.y && b.y}; }
+template <typename T> __device__ __forceinline__ T sel(bool m, T a, T b) { return m ? a : b; }
+__device__ __forceinline__ V2 sel(B2 m, V2 a, V2 b) { return mk2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y); }
+
+// Reciprocal, reciprocal square root and square root (of a non-negative value). FP32 uses
+// the fast hardware approximations; FP64 the correctly rounded operations.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ V2 rcp(V2 x) { return mk2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ V2 rsq(V2 x) { return mk2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
+__device__ __forceinline__ float sqrt0(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt0(double x) { return sqrt(x); }
+__device__ __forceinline__ V2 sqrt0(V2 x) { return mk2(sqrtf(x.v.x), sqrtf(x.v.y)); }
+
+// sgn with sgn(0) = 0.
+template <typename V> __device__ __forceinline__ V sgnv(V a)
 {
-    if (phi >= T(1)) return T(1);
-    T p2 = phi * phi, t = T(1) - p2;
-    return tmin(phi * sqrt(T(4) + t * t) / (T(1) + p2), T(1));
+    const V z = splat<V>(0);
+    return sel(gt(a, z), splat<V>(1), sel(lt(a, z), splat<V>(-1), z));
+}
+template <typename V> __device__ __forceinline__ V pow8(V a) { V a2 = a * a, a4 = a2 * a2; return a4 * a4; }
+
+// Eq. 98: f(phi) = min(phi sqrt(4 + (1 - phi^2)^2) / (1 + phi^2), 1). The argument is clamped
+// at 2 (f = 1 for every phi >= 1, and the clamp keeps the powers below in range), and the
+// square root and the division share one reciprocal square root:
+// sqrt(s) / q = s / sqrt(s q^2) with s = 4 + (1 - phi^2)^2, q = 1 + phi^2.
+template <typename V> __device__ __forceinline__ V fmach(V phi)
+{
+    const V one = splat<V>(1);
+    const V p = vmin(phi, splat<V>(2));
+    const V p2 = p * p;
+    const V t = one - p2;
+    const V s = vfma(t, t, splat<V>(4));
+    const V q = one + p2;
+    return vmin(p * s * rsq(s * q * q), one);
+}
+
+// Eq. 95 (with P values of Eq. 97 already reduced to their minimum a by Eq. 96).
+template <typename V> __device__ __forceinline__ V detector_of(V a)
+{
+    return sel(ge(a, splat<V>(1)), splat<V>(1), pow8(fmach(a)));
 }
 
 // Mirror image of a velocity about a unit normal (wall ghost state).
@@ -43,127 +117,109 @@ template <typename T> __device__ __forceinline__ void mirror_vel(T &u, T &v, T n
     v -= T(2) * un * ny;
 }
 
-// Scheme constants of one grid in the working precision.
-template <typename T> struct Coef {
-    T g, gm1, gm1i, mr2, rr_thr, eps2;
-    int eps1, xi_form;
-};
+// ------------------------------------------------------------------ the Roe-AM flux
+// Quantities of one side of a face, in the face frame: un is the velocity along the unit
+// normal (from L to R), ut the tangential one. c2 = gamma p / rho, H total enthalpy,
+// sr = sqrt(rho), Mq = |q| / c.
+template <typename V> struct FS { V r, un, ut, p, c2, H, sr, Mq; };
 
-template <typename T> __device__ __forceinline__ Coef<T> make_coef(const GridDev &G)
+template <typename V, typename S>
+__device__ __forceinline__ FS<V> side_from_prims(V r, V un, V ut, V p, const GridCoef<S> &K)
 {
-    Coef<T> c;
-    c.g = T(G.gamma);
-    c.gm1 = T(G.gamma - 1.0);
-    c.gm1i = T(1.0 / (G.gamma - 1.0));
-    c.mr2 = T(G.m_ref * G.m_ref);
-    c.rr_thr = T(1e-5 * G.u_ref);
-    c.eps2 = T(G.eps2);
-    c.eps1 = G.eps1;
-    c.xi_form = G.xi_form;
-    return c;
-}
-
-// Per-side quantities of a face state W = (rho, u, v, p).
-template <typename T> struct Side { T r, u, v, p, c2, H, sr, Un, Mq; };
-
-template <typename T> __device__ __forceinline__ Side<T> make_side(T r, T u, T v, T p, T nx, T ny, const Coef<T> &K)
-{
-    Side<T> s;
-    s.r = r; s.u = u; s.v = v; s.p = p;
-    s.c2 = K.g * p / r;
-    T q2 = u * u + v * v;
-    s.H = s.c2 * K.gm1i + T(0.5) * q2;
-    s.sr = sqrt(r);
-    s.Un = nx * u + ny * v;
-    s.Mq = sqrt(q2 / s.c2);    // |q| / c
+    FS<V> s;
+    s.r = r; s.un = un; s.ut = ut; s.p = p;
+    const V ri = rcp(r);
+    s.c2 = splat<V>(K.g) * p * ri;
+    const V q2 = vfma(un, un, ut * ut);
+    s.H = vfma(s.c2, splat<V>(K.gm1i), splat<V>(S(0.5)) * q2);
+    s.sr = r * rsq(r);
+    s.Mq = sqrt0(q2 * rcp(s.c2));
     return s;
 }
 
-// Roe-AM numerical flux per unit face length (Section 6.2), unit normal n from L to R.
-template <typename T>
-__device__ __forceinline__ void roeam_flux(const Side<T> &L, const Side<T> &R, T nx, T ny, T s1, const Coef<T> &K,
-                                           T F[4])
+// Twice the Roe-AM numerical flux per unit face length, in the face frame (components:
+// mass, normal momentum, tangential momentum, energy). Section 6.2, term by term:
+// central part (Eqs. 3-4), Roe averages, M (Eq. 93), Mbar (Eq. 94), f (Eq. 98), |U|'
+// (Eq. 92, clamped at 0), xi (Eq. 86 with the Eq. 68 factor unless xi_form = 1; the eps1
+// floor with Eqs. 102-109), delta p_p + delta p_u (Eqs. 87-88), rho delta U_p (Eq. 89 with
+// Eqs. 99-101), delta U_u (Eqs. 90-91), assembled as Eq. 85 with the energy convention of
+// Eq. 49.
+template <typename V, typename S>
+__device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1, const GridCoef<S> &K, int eps1,
+                                            int xi_form, V F[4])
 {
-    // Central term, Eqs. 3-4.
-    const T mL = L.r * L.Un, mR = R.r * R.Un;
-    T Fc0 = T(0.5) * (mL + mR);
-    T Fc1 = T(0.5) * (mL * L.u + L.p * nx + mR * R.u + R.p * nx);
-    T Fc2 = T(0.5) * (mL * L.v + L.p * ny + mR * R.v + R.p * ny);
-    T Fc3 = T(0.5) * (mL * L.H + mR * R.H);
+    const V zero = splat<V>(0), one = splat<V>(1), half = splat<V>(S(0.5));
+    const V mL = L.r * L.un, mR = R.r * R.un;
+    const V F0c = mL + mR;
+    const V F1c = vfma(mL, L.un, vfma(mR, R.un, L.p + R.p));
+    const V F2c = vfma(mL, L.ut, mR * R.ut);
+    const V F3c = vfma(mL, L.H, mR * R.H);
 
     // Roe averages; c^2 in the sum-of-positives form (no cancellation at high Mach).
-    const T w = T(1) / (L.sr + R.sr);
-    const T rh = L.sr * R.sr;
-    const T uh = (L.sr * L.u + R.sr * R.u) * w;
-    const T vh = (L.sr * L.v + R.sr * R.v) * w;
-    const T Hh = (L.sr * L.H + R.sr * R.H) * w;
-    const T du = R.u - L.u, dv = R.v - L.v;
-    const T c2h = (L.sr * L.c2 + R.sr * R.c2) * w + T(0.5) * K.gm1 * rh * w * w * (du * du + dv * dv);
-    const T ch = sqrt(c2h);
-    const T chi = T(1) / ch;
-    const T Uh = nx * uh + ny * vh;
-    const T aU = tabs(Uh);
+    const V w = rcp(L.sr + R.sr);
+    const V rh = L.sr * R.sr;
+    const V uh = vfma(L.sr, L.un, R.sr * R.un) * w;
+    const V vh = vfma(L.sr, L.ut, R.sr * R.ut) * w;
+    const V Hh = vfma(L.sr, L.H, R.sr * R.H) * w;
+    const V du = R.un - L.un, dv = R.ut - L.ut;
+    const V dq2 = vfma(du, du, dv * dv);
+    const V c2h = vfma(vfma(L.sr, L.c2, R.sr * R.c2), w, splat<V>(K.hgm1) * rh * w * w * dq2);
+    const V chi = rsq(c2h);
+    const V ch = c2h * chi;
+    const V aU = vabs(uh);
 
-    const T M = T(0.5) * (L.Mq + R.Mq);         // Eq. 93
-    const T Mb = aU * chi;                       // Eq. 94
-    const T fM = fmach(M), fMb = fmach(Mb);
-    const T fM8 = pow8(fM), fMb8 = pow8(fMb);
-    const T dUn = R.Un - L.Un, dp = R.p - L.p;
+    const V M = half * (L.Mq + R.Mq);
+    const V Mb = aU * chi;
+    const V fM = fmach(M), fMb = fmach(Mb);
+    const V fM8 = pow8(fM), fMb8 = pow8(fMb);
+    const V dp = R.p - L.p;
 
-    // Eq. 92, clamped at zero.
-    const T e = tmax(dUn, T(0));
-    T Up = aU - fMb * (sgn(Uh + ch) - sgn(Uh - ch)) * e * T(0.25);
-    Up = tmax(Up, T(0));
+    // |U|': the bracket sgn(U + c) - sgn(U - c) is 2 for |U| < c, 1 for |U| = c, 0 above.
+    const V br = sel(lt(aU, ch), splat<V>(2), sel(eq(aU, ch), one, zero));
+    const V Up = sel(gt(du, zero), vmax(vfma(splat<V>(S(-0.25)) * fMb * br, du, aU), zero), aU);
 
-    // Eq. 86 (with the Eq. 68 factor unless xi_form = 1).
-    const T xfac = K.xi_form ? T(1) : T(1) - fMb8;
-    T xi = tabs(T(0.5) * (R.Un + L.Un)) + xfac * T(0.5) * dUn;
-    if (K.eps1) {
-        const T fef = K.eps2 * ch;                                   // Eq. 102
-        const T dq = sqrt(du * du + dv * dv);
-        T n1x = nx, n1y = ny;
-        if (!(dq < K.rr_thr)) { const T dqi = T(1) / dq; n1x = du * dqi; n1y = dv * dqi; }   // Eq. 108
-        const T sk = sgn(n1x * ny - n1y * nx);
-        const T n2x = -sk * n1y, n2y = sk * n1x;                     // Eq. 109 (unit length)
-        const T frr = tabs((n1x * nx + n1y * ny) * (n1x * uh + n1y * vh)) +
-                      tabs((n2x * nx + n2y * ny) * (n2x * uh + n2y * vh));   // Eqs. 103-107
-        xi = tmax(xi, (T(1) - fMb8) * fM8 * tmin(fef, frr));
+    const V xfac = xi_form ? one : one - fMb8;
+    V xi = vmax(vfma(xfac * half, du, vabs(half * (L.un + R.un))), zero);
+    if (eps1) {
+        // Rotated-Riemann estimate in the face frame (n = (1, 0)): n1 = dq / |dq| unless
+        // |dq| < 1e-5 U_ref; |alpha1 U1| + |alpha2 U2| with the unit n2 perpendicular to n1.
+        const V dq = sqrt0(dq2);
+        const auto big = ge(dq, splat<V>(K.rr_thr));
+        const V dqi = rcp(sel(big, dq, one));
+        const V n1x = sel(big, du * dqi, one), n1y = sel(big, dv * dqi, zero);
+        const V frr = vabs(n1x * vfma(n1x, uh, n1y * vh)) + vabs(n1y * (vfma(n1x, vh, -(n1y * uh))));
+        xi = vmax(xi, (one - fMb8) * fM8 * vmin(splat<V>(K.eps2) * ch, frr));
     }
-    xi = tmax(xi, T(0));
 
-    const T mn = tmin(Up, ch);
-    const T dpp = sgn(Uh) * mn * dp * chi;                                       // Eq. 87
-    const T dpu = (T(1) - s1 + s1 * fM) * tmax(ch - Up, T(0)) * rh * dUn;       // Eq. 88
-    T dUp = T(0);                                                                // Eq. 89
-    const T sw = s1 * (T(1) - fM8);
-    if (sw != T(0) && dp != T(0)) {
-        const T theta = tmin(tmax(K.mr2, M * M), T(1));                          // Eq. 101
-        const T om = T(1) - theta;
-        const T ct = T(0.5) * sqrt(T(4) * c2h * theta + om * om * Uh * Uh);      // Eq. 99
-        const T Ut = T(0.5) * (T(1) + theta) * Uh;                               // Eq. 100
-        dUp = sw * (tmax(ct - Up, T(0)) + om * (Up - Uh / (T(2) * ct) * sgn(Ut) * tmin(tabs(Ut), ct))) * dp /
-              (rh * theta * c2h);
-    }
-    const T dUu = T(0.5) * sgn(Uh) * mn * dUn * chi;                            // Eqs. 90-91
+    const V mn = vmin(Up, ch);
+    const V smc = sgnv(uh) * mn * chi;
+    const V pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmax(ch - Up, zero) * rh * du);
+    const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
+    const V om = one - th;
+    const V X = vfma(splat<V>(4) * c2h, th, om * om * uh * uh);
+    const V rX = rsq(X);           // 1 / (2 c~)
+    const V ct = half * X * rX;    // c~
+    const V Ut = half * (one + th) * uh;
+    const V term = vfma(om, Up - uh * rX * sgnv(Ut) * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
+    const V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
+    const V dUu = half * smc * du;
 
-    // Eq. 85 with the energy convention of Eq. 49.
-    const T pp = dpp + dpu;
-    const T QL0 = L.r, QL1 = L.r * L.u, QL2 = L.r * L.v, QL3 = L.r * L.H;
-    const T QR0 = R.r, QR1 = R.r * R.u, QR2 = R.r * R.v, QR3 = R.r * R.H;
-    F[0] = Fc0 - T(0.5) * (xi * (QR0 - QL0) + dUp * rh + dUu * (QR0 + QL0));
-    F[1] = Fc1 - T(0.5) * (xi * (QR1 - QL1) + pp * nx + dUp * rh * uh + dUu * (QR1 + QL1));
-    F[2] = Fc2 - T(0.5) * (xi * (QR2 - QL2) + pp * ny + dUp * rh * vh + dUu * (QR2 + QL2));
-    F[3] = Fc3 - T(0.5) * (xi * (QR3 - QL3) + dUp * rh * Hh + dUu * (QR3 + QL3));
+    const V QL2 = L.r * L.ut, QR2 = R.r * R.ut, QL3 = L.r * L.H, QR3 = R.r * R.H;
+    F[0] = F0c - vfma(xi, R.r - L.r, vfma(dUu, R.r + L.r, A));
+    F[1] = F1c - vfma(xi, mR - mL, vfma(dUu, mR + mL, vfma(A, uh, pp)));
+    F[2] = F2c - vfma(xi, QR2 - QL2, vfma(dUu, QR2 + QL2, A * vh));
+    F[3] = F3c - vfma(xi, QR3 - QL3, vfma(dUu, QR3 + QL3, A * Hh));
 }
 
 // Largest dissipative signal speed normal to a face: |U| + max(c, c~/theta), Eqs. 99-101 on
 // the cell state (classical |U| + c when theta = 1).
 template <typename T> __device__ __forceinline__ T signal_speed(T Un, T c, T q2, T mr2)
 {
-    const T th = tmin(tmax(mr2, q2 / (c * c)), T(1));
+    const T th = vmin(vmax(mr2, q2 / (c * c)), T(1));
+    if (th >= T(1)) return vabs(Un) + c;
     const T om = T(1) - th;
     const T ct = T(0.5) * sqrt(T(4) * c * c * th + om * om * Un * Un);
-    return tabs(Un) + tmax(c, ct / th);
+    return vabs(Un) + vmax(c, ct / th);
 }
 
 // ------------------------------------------------------------------ geometry
@@ -186,379 +242,583 @@ __device__ __forceinline__ CellGeom<T> cell_geom(T x00, T x10, T x01, T x11, T y
     return c;
 }
 
-template <typename T>
-__device__ __forceinline__ T cell_rate(T r, T u, T v, T p, const CellGeom<T> &cg, const Coef<T> &K)
+template <bool CURV, typename T>
+__device__ __forceinline__ T cell_rate(T r, T u, T v, T p, const CellGeom<T> &cg, const GridCoef<T> &K)
 {
     const T c = sqrt(K.g * p / r);
     const T q2 = u * u + v * v;
-    const T lx = sqrt(cg.Xx * cg.Xx + cg.Xy * cg.Xy), ly = sqrt(cg.Yx * cg.Yx + cg.Yy * cg.Yy);
-    const T sx = signal_speed((u * cg.Xx + v * cg.Xy) / lx, c, q2, K.mr2);
-    const T sy = signal_speed((u * cg.Yx + v * cg.Yy) / ly, c, q2, K.mr2);
-    return (sx * lx + sy * ly) / cg.V;
-}
-
-__device__ __forceinline__ int find_grid(const int *tile_base, int ngrids, int t)
-{
-    int lo = 0, hi = ngrids - 1;   // largest g with tile_base[g] <= t
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(tile_base + mid) <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
-
-// State of cell (i, j) of grid G for i in [-2, ni+1], j in [-2, nj+1] as primitives, from
-// the interior or, outside it, from the boundary conditions: the i direction is resolved
-// first, then j; a WALL side mirrors the velocity about the boundary face normal. flag bit 0:
-// the resolved cell is solid; bit 1: a WALL side produced it. Indices beyond the two ghost
-// layers (ragged tiles) are clamped into the grid; their values are never used.
-template <typename T, bool CURV>
-__device__ __forceinline__ void load_ext(const StageArgs<T> &a, const GridDev &G, int i, int j, T w[4], uint8_t &fl)
-{
-    const int ni = G.ni, nj = G.nj;
-    int ii = i, jj = j, mx = 0, my = 0;
-    bool inflow = false;
-    if (i < 0 || i >= ni) {
-        const int bc = G.bc[i < 0 ? 0 : 1];
-        if (bc == BC_INFLOW) inflow = true;
-        else if (bc == BC_PERIODIC) ii = ((i % ni) + ni) % ni;
-        else if (bc == BC_OUTFLOW) ii = i < 0 ? 0 : ni - 1;
-        else { ii = i < 0 ? -1 - i : 2 * ni - 1 - i; mx = i < 0 ? 1 : 2; }
-    }
-    if (!inflow && (j < 0 || j >= nj)) {
-        const int bc = G.bc[j < 0 ? 2 : 3];
-        if (bc == BC_INFLOW) inflow = true;
-        else if (bc == BC_PERIODIC) jj = ((j % nj) + nj) % nj;
-        else if (bc == BC_OUTFLOW) jj = j < 0 ? 0 : nj - 1;
-        else { jj = j < 0 ? -1 - j : 2 * nj - 1 - j; my = j < 0 ? 1 : 2; }
-    }
-    ii = clampi(ii, 0, ni - 1);
-    jj = clampi(jj, 0, nj - 1);
-    fl = 0;
-    if (inflow) {
-        w[0] = T(G.inflow[0]); w[1] = T(G.inflow[1]); w[2] = T(G.inflow[2]); w[3] = T(G.inflow[3]);
+    if constexpr (CURV) {
+        const T lx = sqrt(cg.Xx * cg.Xx + cg.Xy * cg.Xy), ly = sqrt(cg.Yx * cg.Yx + cg.Yy * cg.Yy);
+        const T sx = signal_speed((u * cg.Xx + v * cg.Xy) / lx, c, q2, K.mr2);
+        const T sy = signal_speed((u * cg.Yx + v * cg.Yy) / ly, c, q2, K.mr2);
+        return (sx * lx + sy * ly) / cg.V;
     } else {
-        const long long c = G.off + (long long)jj * G.pitch + ii;
-        const T r = a.src[c], ru = a.src[c + G.plane], rv = a.src[c + 2 * G.plane], rE = a.src[c + 3 * G.plane];
-        const T u = ru / r, v = rv / r;
-        w[0] = r; w[1] = u; w[2] = v;
-        w[3] = T(G.gamma - 1.0) * (rE - T(0.5) * r * (u * u + v * v));
-        if (G.soff >= 0 && a.solid[G.soff + (long long)jj * ni + ii]) fl |= 1;
+        return signal_speed(u, c, q2, K.mr2) / K.dx + signal_speed(v, c, q2, K.mr2) / K.dy;
     }
-    if (my) {
-        T nx = T(0), ny = T(1);
-        if (CURV) {
-            const int J = my == 1 ? 0 : nj;
-            const long long b = G.voff + (long long)J * G.vpitch + ii;
-            const T sx = -(a.vdy[b + 1] - a.vdy[b]), sy = T(G.dx) + (a.vdx[b + 1] - a.vdx[b]);
-            const T l = sqrt(sx * sx + sy * sy);
-            nx = sx / l; ny = sy / l;
-        }
-        mirror_vel(w[1], w[2], nx, ny);
-    }
-    if (mx) {
-        T nx = T(1), ny = T(0);
-        if (CURV) {
-            const int I = mx == 1 ? 0 : ni;
-            const int jr = clampi(j, 0, nj - 1);
-            const long long b = G.voff + (long long)jr * G.vpitch + I;
-            const T sx = T(G.dy) + (a.vdy[b + G.vpitch] - a.vdy[b]), sy = -(a.vdx[b + G.vpitch] - a.vdx[b]);
-            const T l = sqrt(sx * sx + sy * sy);
-            nx = sx / l; ny = sy / l;
-        }
-        mirror_vel(w[1], w[2], nx, ny);
-    }
-    if (mx || my) fl |= 2;
 }
 
-// ------------------------------------------------------------------ shared-memory tile
-template <typename T, int TX, int TY, int H, bool CURV> struct Tile {
-    static constexpr int HX = TX + 2 * H, HY = TY + 2 * H;
-    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-    static constexpr int VX = CURV ? TX + 3 : 1, VY = CURV ? TY + 3 : 1;
-    T W[4][HY][HX];            // primitives of the halo tile; cell (a, b) at [b + H][a + H]
-    T Px[TY + 2][TX + 1];      // Eq. 97 on x-face column c between cells c-1, c; rows b = -1..TY at [b + 1]
-    T Py[TY + 1][TX + 2];      // Eq. 97 on y-face row r between rows r-1, r; columns a = -1..TX at [a + 1]
-    T Fx[4][TY][TX + 1];       // F |S| through x-face column c of row b
-    T Fy[4][TY + 1][TX];       // F |S| through y-face row r of column a
-    T vx[VY][VX], vy[VY][VX];  // vertex displacements, vertices i0-1..i0+TX+1, j0-1..j0+TY+1
-    uint8_t flag[HY][HX];      // bit 0 solid, bit 1 wall ghost
+// Rate slots hold a non-negative rate as the bit pattern of the working precision (float bits
+// in the low word for FP32), so that an unsigned atomicMax orders them like the values.
+__device__ __forceinline__ unsigned long long rate_bits(float r) { return (unsigned long long)__float_as_uint(r); }
+__device__ __forceinline__ unsigned long long rate_bits(double r) { return (unsigned long long)__double_as_longlong(r); }
+template <typename T> __device__ __forceinline__ T rate_value(unsigned long long b);
+template <> __device__ __forceinline__ float rate_value<float>(unsigned long long b) { return __uint_as_float((unsigned)b); }
+template <> __device__ __forceinline__ double rate_value<double>(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Boundary resolution of one index direction: a cell index outside [0, n) maps to the
+// source index of its ghost value and a kind: 0 interior/periodic/outflow (a plain copy of
+// the source cell), 1 WALL (the source cell mirrored about the boundary face), 2 INFLOW (the
+// prescribed state). Indices beyond the two ghost layers (ragged strips) are clamped into the
+// grid; their values are never used.
+__device__ __forceinline__ int resolve_index(int x, int n, int bc_lo, int bc_hi, int &kind)
+{
+    kind = 0;
+    if (x >= 0 && x < n) return x;
+    const int bc = x < 0 ? bc_lo : bc_hi;
+    int s;
+    if (bc == BC_INFLOW) { kind = 2; s = 0; }
+    else if (bc == BC_PERIODIC) s = ((x % n) + n) % n;
+    else if (bc == BC_OUTFLOW) s = x < 0 ? 0 : n - 1;
+    else { kind = 1; s = x < 0 ? -1 - x : 2 * n - 1 - x; }
+    return clampi(s, 0, n - 1);
+}
+
+// ------------------------------------------------------------------ face evaluation
+template <typename T> __device__ __forceinline__ T shup(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+template <typename T> __device__ __forceinline__ T shdn(T v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+template <typename T> __device__ __forceinline__ T ratio_P(T r0, T p0, T r1, T p1)
+{
+    return vmin(vmin(p0, p1) / vmax(p0, p1), vmin(r0, r1) / vmax(r0, r1));   // Eq. 97
+}
+
+// MUSCL limited slope: minmod(a, b) = (sgn a + sgn b)/2 min(|a|, |b|); van Leer
+// (a|b| + |a|b) / (|a| + |b|), 0 when ab <= 0.
+template <typename V> __device__ __forceinline__ V limiter(bool vanleer, V a, V b)
+{
+    const V zero = splat<V>(0);
+    if (vanleer) {
+        const auto keep = gt(a * b, zero);
+        const V aa = vabs(a), ab = vabs(b);
+        return sel(keep, vfma(a, ab, aa * b) * rcp(sel(keep, aa + ab, splat<V>(1))), zero);
+    }
+    return sel(gt(a * b, zero), sel(gt(a, zero), vmin(a, b), vmax(a, b)), zero);
+}
+
+// Cell-window entry: primitives (rho, u, v, p) in the global frame, the derived face
+// quantities (first order: computed once per cell), and the flags (bit 0 solid, bit 1 wall).
+template <typename T> struct WC {
+    T r, u, v, p, c2, H, sr, Mq;
+    uint8_t fl;
 };
 
-// Smallest sizeof that holds a tile of each variant (dynamic shared memory per CTA).
-template <typename T, int TX, int TY, bool MUSCL, bool CURV>
-constexpr size_t tile_smem_bytes() { return sizeof(Tile<T, TX, TY, MUSCL ? 2 : 1, CURV>); }
-
-template <typename T> __device__ __forceinline__ unsigned long long rate_bits(T r)
+template <typename T, bool MUSCL>
+__device__ __forceinline__ void derive(WC<T> &c, const GridCoef<T> &K)
 {
-    return (unsigned long long)__double_as_longlong((double)r);
+    if constexpr (!MUSCL) {
+        const FS<T> s = side_from_prims(c.r, c.u, c.v, c.p, K);
+        c.c2 = s.c2; c.H = s.H; c.sr = s.sr; c.Mq = s.Mq;
+    } else {
+        c.c2 = c.H = c.sr = c.Mq = T(0);
+    }
 }
 
-// Block-wide max of a non-negative value (all threads must call).
-template <int NT> __device__ __forceinline__ double block_max(double v, double *red)
+// A face as seen by one lane: left/right cells A, B, MUSCL stencil cells Am (before A) and
+// Bp (after B), the unit normal from A to B, the length, the unit normals of the faces Am|A
+// and B|Bp (for mirrors at solid stencil cells), and the detector value.
+template <typename T> struct Face {
+    WC<T> A, B, Am, Bp;
+    T nx, ny, len, nAmx, nAmy, nBpx, nBpy, s1;
+};
+
+template <typename T> __device__ __forceinline__ bool face_is_wall(const Face<T> &f, bool muscl)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x < 32) {
-        r = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    return (f.A.fl | f.B.fl) != 0 || (muscl && ((f.Am.fl | f.Bp.fl) & 1));
+}
+
+// Face-frame side from global primitives (rotation by the face normal).
+template <typename V, typename S>
+__device__ __forceinline__ FS<V> side_rot(V r, V u, V v, V p, V nx, V ny, const GridCoef<S> &K)
+{
+    return side_from_prims(r, vfma(nx, u, ny * v), vfma(nx, v, -(ny * u)), p, K);
+}
+
+// Reconstructed (or first-order) face states of one face in the global frame, with the
+// positivity fallback; returns false when an FP32 value within rounding of zero needs the
+// FP64 decision (taken here) — the caller is then on the scalar path anyway.
+template <typename V, typename S>
+__device__ __forceinline__ void muscl_states(bool vanleer, const V Am[4], const V A[4], const V B[4], const V Bp[4],
+                                             V WL[4], V WR[4])
+{
+    const V half = splat<V>(S(0.5)), zero = splat<V>(0);
+    V rL[4], rR[4];
+    for (int k = 0; k < 4; ++k) {
+        rL[k] = vfma(half, limiter(vanleer, A[k] - Am[k], B[k] - A[k]), A[k]);
+        rR[k] = B[k] - half * limiter(vanleer, B[k] - A[k], Bp[k] - B[k]);
     }
-    return r;   // valid in thread 0
+    const auto pos = gt(rL[0], zero) && gt(rL[3], zero) && gt(rR[0], zero) && gt(rR[3], zero);
+    for (int k = 0; k < 4; ++k) { WL[k] = sel(pos, rL[k], A[k]); WR[k] = sel(pos, rR[k], B[k]); }
+}
+
+// Scalar evaluation of one face: walls (first-order state and its mirror), MUSCL with solid
+// mirrors and the FP64 positivity decision in FP32, rotation to the face frame, flux, and the
+// rotation back. Returns F |S| in the global frame.
+template <typename T, bool MUSCL>
+__device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> &K, int eps1, int xi_form,
+                                            bool vanleer, T F[4])
+{
+    F[0] = F[1] = F[2] = F[3] = T(0);
+    if ((f.A.fl & f.B.fl) & 1) return;
+    T WL[4] = {f.A.r, f.A.u, f.A.v, f.A.p}, WR[4] = {f.B.r, f.B.u, f.B.v, f.B.p};
+    if ((f.A.fl | f.B.fl) != 0) {
+        if (f.A.fl) { for (int k = 0; k < 4; ++k) WL[k] = WR[k]; mirror_vel(WL[1], WL[2], f.nx, f.ny); }
+        else { for (int k = 0; k < 4; ++k) WR[k] = WL[k]; mirror_vel(WR[1], WR[2], f.nx, f.ny); }
+    } else if constexpr (MUSCL) {
+        T M0[4] = {f.Am.r, f.Am.u, f.Am.v, f.Am.p}, M3[4] = {f.Bp.r, f.Bp.u, f.Bp.v, f.Bp.p};
+        if (f.Am.fl & 1) { for (int k = 0; k < 4; ++k) M0[k] = WL[k]; mirror_vel(M0[1], M0[2], f.nAmx, f.nAmy); }
+        if (f.Bp.fl & 1) { for (int k = 0; k < 4; ++k) M3[k] = WR[k]; mirror_vel(M3[1], M3[2], f.nBpx, f.nBpy); }
+        T lL[4], lR[4], rL[4], rR[4];
+        for (int k = 0; k < 4; ++k) {
+            lL[k] = limiter(vanleer, WL[k] - M0[k], WR[k] - WL[k]);
+            lR[k] = limiter(vanleer, WR[k] - WL[k], M3[k] - WR[k]);
+            rL[k] = WL[k] + T(0.5) * lL[k];
+            rR[k] = WR[k] - T(0.5) * lR[k];
+        }
+        // Positivity of the reconstructed density and pressure, else first order. In FP32 a
+        // value within rounding of zero is re-decided exactly in FP64.
+        bool pos = rL[0] > T(0) && rL[3] > T(0) && rR[0] > T(0) && rR[3] > T(0);
+        if (sizeof(T) == 4 && pos) {
+            const T eps = T(1e-6);
+            if (rL[0] < eps * WL[0] || rL[3] < eps * WL[3] || rR[0] < eps * WR[0] || rR[3] < eps * WR[3])
+                pos = ((double)WL[0] + 0.5 * (double)lL[0] > 0.0) && ((double)WL[3] + 0.5 * (double)lL[3] > 0.0) &&
+                      ((double)WR[0] - 0.5 * (double)lR[0] > 0.0) && ((double)WR[3] - 0.5 * (double)lR[3] > 0.0);
+        }
+        if (pos) for (int k = 0; k < 4; ++k) { WL[k] = rL[k]; WR[k] = rR[k]; }
+    }
+    FS<T> L, R;
+    if (!MUSCL && (f.A.fl | f.B.fl) == 0) {
+        L = {f.A.r, vfma(f.nx, f.A.u, f.ny * f.A.v), vfma(f.nx, f.A.v, -(f.ny * f.A.u)), f.A.p, f.A.c2, f.A.H, f.A.sr, f.A.Mq};
+        R = {f.B.r, vfma(f.nx, f.B.u, f.ny * f.B.v), vfma(f.nx, f.B.v, -(f.ny * f.B.u)), f.B.p, f.B.c2, f.B.H, f.B.sr, f.B.Mq};
+    } else {
+        L = side_rot(WL[0], WL[1], WL[2], WL[3], f.nx, f.ny, K);
+        R = side_rot(WR[0], WR[1], WR[2], WR[3], f.nx, f.ny, K);
+    }
+    T G2[4];
+    roeam_flux2(L, R, f.s1, K, eps1, xi_form, G2);
+    const T h = T(0.5) * f.len;
+    F[0] = h * G2[0];
+    F[1] = h * (f.nx * G2[1] - f.ny * G2[2]);
+    F[2] = h * (f.ny * G2[1] + f.nx * G2[2]);
+    F[3] = h * G2[3];
+}
+
+// Packed FP32 evaluation of a lane's x-face (component x) and y-face (component y), both free
+// of walls. Cartesian faces enter with their normal velocity first (the y-face's (v, u) is a
+// relabelling, undone on output); curvilinear faces are rotated by their normals.
+template <bool MUSCL, bool CURV>
+__device__ __forceinline__ void faces_packed(const Face<float> &fx, const Face<float> &fy, const GridCoef<float> &K,
+                                             int eps1, int xi_form, bool vanleer, float Fx[4], float Fy[4])
+{
+    FS<V2> L, R;
+    if constexpr (!MUSCL) {
+        const WC<float> &a = fx.A, &b = fx.B, &c = fy.A, &d = fy.B;
+        if constexpr (CURV) {
+            const V2 nx = mk2(fx.nx, fy.nx), ny = mk2(fx.ny, fy.ny);
+            const V2 uL = mk2(a.u, c.u), vL = mk2(a.v, c.v), uR = mk2(b.u, d.u), vR = mk2(b.v, d.v);
+            L = {mk2(a.r, c.r), vfma(nx, uL, ny * vL), vfma(nx, vL, -(ny * uL)), mk2(a.p, c.p), mk2(a.c2, c.c2),
+                 mk2(a.H, c.H), mk2(a.sr, c.sr), mk2(a.Mq, c.Mq)};
+            R = {mk2(b.r, d.r), vfma(nx, uR, ny * vR), vfma(nx, vR, -(ny * uR)), mk2(b.p, d.p), mk2(b.c2, d.c2),
+                 mk2(b.H, d.H), mk2(b.sr, d.sr), mk2(b.Mq, d.Mq)};
+        } else {
+            L = {mk2(a.r, c.r), mk2(a.u, c.v), mk2(a.v, c.u), mk2(a.p, c.p), mk2(a.c2, c.c2), mk2(a.H, c.H),
+                 mk2(a.sr, c.sr), mk2(a.Mq, c.Mq)};
+            R = {mk2(b.r, d.r), mk2(b.u, d.v), mk2(b.v, d.u), mk2(b.p, d.p), mk2(b.c2, d.c2), mk2(b.H, d.H),
+                 mk2(b.sr, d.sr), mk2(b.Mq, d.Mq)};
+        }
+    } else {
+        const V2 Am[4] = {mk2(fx.Am.r, fy.Am.r), mk2(fx.Am.u, fy.Am.u), mk2(fx.Am.v, fy.Am.v), mk2(fx.Am.p, fy.Am.p)};
+        const V2 A[4] = {mk2(fx.A.r, fy.A.r), mk2(fx.A.u, fy.A.u), mk2(fx.A.v, fy.A.v), mk2(fx.A.p, fy.A.p)};
+        const V2 B[4] = {mk2(fx.B.r, fy.B.r), mk2(fx.B.u, fy.B.u), mk2(fx.B.v, fy.B.v), mk2(fx.B.p, fy.B.p)};
+        const V2 Bp[4] = {mk2(fx.Bp.r, fy.Bp.r), mk2(fx.Bp.u, fy.Bp.u), mk2(fx.Bp.v, fy.Bp.v), mk2(fx.Bp.p, fy.Bp.p)};
+        V2 WL[4], WR[4];
+        muscl_states<V2, float>(vanleer, Am, A, B, Bp, WL, WR);
+        if constexpr (CURV) {
+            const V2 nx = mk2(fx.nx, fy.nx), ny = mk2(fx.ny, fy.ny);
+            L = side_rot(WL[0], WL[1], WL[2], WL[3], nx, ny, K);
+            R = side_rot(WR[0], WR[1], WR[2], WR[3], nx, ny, K);
+        } else {
+            L = side_from_prims(WL[0], mk2(WL[1].v.x, WL[2].v.y), mk2(WL[2].v.x, WL[1].v.y), WL[3], K);
+            R = side_from_prims(WR[0], mk2(WR[1].v.x, WR[2].v.y), mk2(WR[2].v.x, WR[1].v.y), WR[3], K);
+        }
+    }
+    V2 G2[4];
+    roeam_flux2(L, R, mk2(fx.s1, fy.s1), K, eps1, xi_form, G2);
+    const float hx = 0.5f * fx.len, hy = 0.5f * fy.len;
+    Fx[0] = hx * G2[0].v.x;
+    Fx[3] = hx * G2[3].v.x;
+    Fy[0] = hy * G2[0].v.y;
+    Fy[3] = hy * G2[3].v.y;
+    if constexpr (CURV) {
+        Fx[1] = hx * (fx.nx * G2[1].v.x - fx.ny * G2[2].v.x);
+        Fx[2] = hx * (fx.ny * G2[1].v.x + fx.nx * G2[2].v.x);
+        Fy[1] = hy * (fy.nx * G2[1].v.y - fy.ny * G2[2].v.y);
+        Fy[2] = hy * (fy.ny * G2[1].v.y + fy.nx * G2[2].v.y);
+    } else {
+        Fx[1] = hx * G2[1].v.x;
+        Fx[2] = hx * G2[2].v.x;
+        Fy[1] = hy * G2[2].v.y;
+        Fy[2] = hy * G2[1].v.y;
+    }
 }
 
 // ------------------------------------------------------------------ the fused stage kernel
-template <typename T, int TX, int TY, int NT, bool MUSCL, bool CURV>
-__global__ void __launch_bounds__(NT) stage_kernel(const StageArgs<T> a)
+// Per-grid values a warp keeps in registers while it sweeps a strip.
+template <typename T> struct GridRegs {
+    const T *src, *un;
+    T *dst;
+    const T *vdx, *vdy;         // vertex displacement planes of this grid (curvilinear)
+    const uint8_t *solid;       // solid mask of this grid, or null
+    int ni, nj, pitch, plane, vpitch;
+    int bcW, bcE, bcS, bcN;
+};
+
+// Loading a cell is split in two so that the next row's HBM loads are in flight while the
+// current row is computed: issue_cell resolves row j (the column is resolved once per unit
+// into isrc / kx) and starts the loads; finish_cell turns them into primitives, derived face
+// quantities and flags. Resolution order: an INFLOW side in i gives the inflow state;
+// otherwise an INFLOW side in j gives it (then mirrored by a WALL side in i); otherwise the
+// source cell, mirrored about the S/N boundary face by a WALL side in j, then about the W/E
+// boundary face by a WALL side in i.
+template <typename T> struct Pending {
+    T raw[4];
+    int jsrc, ky;
+};
+
+template <typename T>
+__device__ __forceinline__ void issue_cell(const GridRegs<T> &R, int isrc, int kx, int j, Pending<T> &q)
+{
+    q.jsrc = resolve_index(j, R.nj, R.bcS, R.bcN, q.ky);
+    if (kx != 2 && q.ky != 2) {
+        const int x = q.jsrc * R.pitch + isrc;
+        q.raw[0] = __ldg(R.src + x);
+        q.raw[1] = __ldg(R.src + x + R.plane);
+        q.raw[2] = __ldg(R.src + x + 2 * R.plane);
+        q.raw[3] = __ldg(R.src + x + 3 * R.plane);
+    }
+}
+
+template <typename T, bool MUSCL, bool CURV, bool WALLS>
+__device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef<T> &K, int i, int isrc, int kx, int j,
+                                            const Pending<T> &q, WC<T> &c)
+{
+    const int ky = q.ky;
+    c.fl = 0;
+    if (kx == 2 || ky == 2) {
+        c.r = K.inflow[0]; c.u = K.inflow[1]; c.v = K.inflow[2]; c.p = K.inflow[3];
+    } else {
+        const T ri = rcp(q.raw[0]);
+        c.r = q.raw[0]; c.u = q.raw[1] * ri; c.v = q.raw[2] * ri;
+        c.p = K.gm1 * (q.raw[3] - T(0.5) * q.raw[0] * (c.u * c.u + c.v * c.v));
+        if constexpr (WALLS) {
+            if (R.solid && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1;
+        }
+    }
+    if constexpr (WALLS) {
+        if (ky == 1 && kx != 2) {
+            T nx = T(0), ny = T(1);
+            if constexpr (CURV) {
+                const int b = (j < 0 ? 0 : R.nj) * R.vpitch + isrc;
+                const T sx = -(R.vdy[b + 1] - R.vdy[b]), sy = K.dx + (R.vdx[b + 1] - R.vdx[b]);
+                const T l = rsq(sx * sx + sy * sy);
+                nx = sx * l; ny = sy * l;
+            }
+            mirror_vel(c.u, c.v, nx, ny);
+        }
+        if (kx == 1) {
+            T nx = T(1), ny = T(0);
+            if constexpr (CURV) {
+                const int b = clampi(j, 0, R.nj - 1) * R.vpitch + (i < 0 ? 0 : R.ni);
+                const T sx = K.dy + (R.vdy[b + R.vpitch] - R.vdy[b]), sy = -(R.vdx[b + R.vpitch] - R.vdx[b]);
+                const T l = rsq(sx * sx + sy * sy);
+                nx = sx * l; ny = sy * l;
+            }
+            mirror_vel(c.u, c.v, nx, ny);
+        }
+        if ((kx == 1 || ky == 1) && kx != 2) c.fl |= 2;
+    }
+    derive<T, MUSCL>(c, K);
+}
+
+template <typename T> __device__ __forceinline__ WC<T> shup_c(const WC<T> &c, int d, bool derived)
+{
+    WC<T> o;
+    o.r = shup(c.r, d); o.u = shup(c.u, d); o.v = shup(c.v, d); o.p = shup(c.p, d);
+    if (derived) { o.c2 = shup(c.c2, d); o.H = shup(c.H, d); o.sr = shup(c.sr, d); o.Mq = shup(c.Mq, d); }
+    else { o.c2 = o.H = o.sr = o.Mq = T(0); }
+    o.fl = (uint8_t)__shfl_up_sync(0xffffffffu, (int)c.fl, d);
+    return o;
+}
+template <typename T> __device__ __forceinline__ WC<T> shdn_c(const WC<T> &c, int d)
+{
+    WC<T> o;
+    o.r = shdn(c.r, d); o.u = shdn(c.u, d); o.v = shdn(c.v, d); o.p = shdn(c.p, d);
+    o.c2 = o.H = o.sr = o.Mq = T(0);
+    o.fl = (uint8_t)__shfl_down_sync(0xffffffffu, (int)c.fl, d);
+    return o;
+}
+
+template <typename T, bool MUSCL, bool CURV, bool WALLS, int NT>
+__global__ void __launch_bounds__(NT, STAGE_MIN_BLOCKS) stage_kernel(const StageArgs<T> a)
 {
     constexpr int H = MUSCL ? 2 : 1;
-    using TL = Tile<T, TX, TY, H, CURV>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TL &S = *reinterpret_cast<TL *>(smem_raw);
-    __shared__ double red[NT / 32];
-    const int tid = threadIdx.x;
+    constexpr int NW = H + 2;          // window rows j-H .. j+1
+    constexpr int NV = 4;              // vertex rows j-1 .. j+2 (curvilinear)
+    constexpr int WIDTH = 32 - 2 * H;  // interior columns per strip
+    constexpr bool PACKED = sizeof(T) == 4;
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (NT / 32);
 
     if (a.rate_zero && blockIdx.x == 0)
-        for (int g = tid; g < a.ngrids; g += NT) a.rate_zero[g] = 0ull;
+        for (int g = threadIdx.x; g < a.ngrids; g += NT) a.rate_zero[g] = 0ull;
 
     double acc_s[4] = {0.0, 0.0, 0.0, 0.0}, acc_m[4] = {0.0, 0.0, 0.0, 0.0};
 
-    for (int t = a.tile_lo + blockIdx.x; t < a.tile_hi; t += gridDim.x) {
-        const int g = find_grid(a.tile_base, a.ngrids, t);
+    for (int u = a.tile_lo + warp; u < a.tile_hi; u += nwarps) {
+        const int4 unit = __ldg(a.units + u);   // (grid, first lane's column, j0, j1)
+        const int g = unit.x;
+        const int i = unit.y + lane;            // this lane's column
+        const int j0 = unit.z, j1 = unit.w;
         const GridDev &G = a.grids[g];
-        const int lt = t - G.tile_base;
-        const int i0 = (lt % G.ntx) * TX, j0 = (lt / G.ntx) * TY;
-        const int ni = G.ni, nj = G.nj;
-        const Coef<T> K = make_coef<T>(G);
-        const T dx = T(G.dx), dy = T(G.dy);
-        const bool has_solid = G.soff >= 0;
-
-        __syncthreads();   // the previous tile's readers of S are done
-        // ---- 1. halo tile of primitives (ghosts from the boundary conditions)
-        for (int idx = tid; idx < TL::HX * TL::HY; idx += NT) {
-            const int la = idx % TL::HX, lb = idx / TL::HX;
-            T w[4];
-            uint8_t fl;
-            load_ext<T, CURV>(a, G, i0 + la - H, j0 + lb - H, w, fl);
-            S.W[0][lb][la] = w[0]; S.W[1][lb][la] = w[1]; S.W[2][lb][la] = w[2]; S.W[3][lb][la] = w[3];
-            S.flag[lb][la] = fl;
-        }
-        if (CURV) {
-            for (int idx = tid; idx < TL::VX * TL::VY; idx += NT) {
-                const int va = idx % TL::VX, vb = idx / TL::VX;
-                const int I = clampi(i0 - 1 + va, 0, ni), J = clampi(j0 - 1 + vb, 0, nj);
-                const long long b = G.voff + (long long)J * G.vpitch + I;
-                S.vx[vb][va] = a.vdx[b];
-                S.vy[vb][va] = a.vdy[b];
-            }
-        }
-        __syncthreads();
-
-        // ---- 2. ratio indicator P (Eq. 97) on the faces the detectors read
-        if (G.use_s1) {
-            for (int idx = tid; idx < (TY + 2) * (TX + 1); idx += NT) {
-                const int c = idx % (TX + 1), bb = idx / (TX + 1) - 1;     // cells (c-1, bb), (c, bb)
-                const int ya = bb + H, xa = c - 1 + H;
-                T P = T(1);
-                if (!((S.flag[ya][xa] | S.flag[ya][xa + 1]) & 1)) {
-                    const T p0 = S.W[3][ya][xa], p1 = S.W[3][ya][xa + 1];
-                    const T r0 = S.W[0][ya][xa], r1 = S.W[0][ya][xa + 1];
-                    P = tmin(tmin(p0, p1) / tmax(p0, p1), tmin(r0, r1) / tmax(r0, r1));
-                }
-                S.Px[bb + 1][c] = P;
-            }
-            for (int idx = tid; idx < (TY + 1) * (TX + 2); idx += NT) {
-                const int aa = idx % (TX + 2) - 1, r = idx / (TX + 2);     // cells (aa, r-1), (aa, r)
-                const int xa = aa + H, ya = r - 1 + H;
-                T P = T(1);
-                if (!((S.flag[ya][xa] | S.flag[ya + 1][xa]) & 1)) {
-                    const T p0 = S.W[3][ya][xa], p1 = S.W[3][ya + 1][xa];
-                    const T r0 = S.W[0][ya][xa], r1 = S.W[0][ya + 1][xa];
-                    P = tmin(tmin(p0, p1) / tmax(p0, p1), tmin(r0, r1) / tmax(r0, r1));
-                }
-                S.Py[r][aa + 1] = P;
-            }
-            __syncthreads();
+        const GridCoef<T> K = a.coef[g];
+        GridRegs<T> R;
+        R.src = a.src + G.off;
+        R.un = a.un + G.off;
+        R.dst = a.dst + G.off;
+        R.ni = G.ni; R.nj = G.nj; R.pitch = G.pitch; R.plane = (int)G.plane;
+        R.bcW = G.bc[0]; R.bcE = G.bc[1]; R.bcS = G.bc[2]; R.bcN = G.bc[3];
+        if constexpr (CURV) { R.vdx = a.vdx + G.voff; R.vdy = a.vdy + G.voff; R.vpitch = G.vpitch; }
+        else { R.vdx = R.vdy = nullptr; R.vpitch = 0; }
+        R.solid = (WALLS && G.soff >= 0) ? a.solid + G.soff : nullptr;
+        const int ni = R.ni, nj = R.nj;
+        const bool use_s1 = G.use_s1 != 0;
+        const int eps1 = G.eps1, xi_form = G.xi_form;
+        const bool vanleer = G.limiter == 2;
+        int kx;
+        const int isrc = resolve_index(i, ni, R.bcW, R.bcE, kx);
+        const bool icol = i >= 0 && i < ni;
+        const bool out_lane = lane >= H && lane < H + WIDTH && icol;
+        T dt = T(0);
+        if (a.mode == MODE_STAGE) {
+            if (a.dt_fixed_t > T(0)) dt = a.dt_fixed_t;
+            else dt = a.cfl_t / rate_value<T>(__ldg(a.rate_rd + g));
         }
 
-        // ---- 3. Roe-AM flux through every x- and y-face of the tile
-        for (int f = tid; f < TL::NFX + TL::NFY; f += NT) {
-            const bool isx = f < TL::NFX;
-            int fa, fb;          // x-face: column c, row b; y-face: column a, row r
-            int Ax, Ay, dxs, dys;   // tile-array index of cell A and the step to B
-            T Sx, Sy;
-            bool inside;
-            if (isx) {
-                fa = f % (TX + 1); fb = f / (TX + 1);
-                inside = (j0 + fb < nj) && (i0 + fa <= ni);
-                Ax = fa - 1 + H; Ay = fb + H; dxs = 1; dys = 0;
-                if (CURV) {
-                    Sx = dy + (S.vy[fb + 2][fa + 1] - S.vy[fb + 1][fa + 1]);
-                    Sy = -(S.vx[fb + 2][fa + 1] - S.vx[fb + 1][fa + 1]);
-                } else { Sx = dy; Sy = T(0); }
+        WC<T> Wn[NW];
+        T Px[NW], Py[NW - 1];
+        T vX[NV], vY[NV];
+        Pending<T> pend;
+        auto vload = [&](int J, T &x, T &y) {
+            if constexpr (CURV) {
+                const int b = clampi(J, 0, nj) * R.vpitch + clampi(i, 0, ni);
+                x = __ldg(R.vdx + b); y = __ldg(R.vdy + b);
+            } else { x = y = T(0); }
+        };
+        auto px_of = [&](const WC<T> &c) {   // Eq. 97 on this lane's west face; 1 at solid sides
+            const T rl = shup(c.r, 1), pl = shup(c.p, 1);
+            if constexpr (WALLS) {
+                const int fl = __shfl_up_sync(0xffffffffu, (int)c.fl, 1);
+                if ((c.fl | fl) & 1) return T(1);
+            }
+            return ratio_P(rl, pl, c.r, c.p);
+        };
+        auto py_of = [&](const WC<T> &lo, const WC<T> &hi) {
+            if constexpr (WALLS) {
+                if ((lo.fl | hi.fl) & 1) return T(1);
+            }
+            return ratio_P(lo.r, lo.p, hi.r, hi.p);
+        };
+        for (int w = 0; w < NW; ++w) {
+            const int jr = j0 - H + w;
+            issue_cell(R, isrc, kx, jr, pend);
+            finish_cell<T, MUSCL, CURV, WALLS>(R, K, i, isrc, kx, jr, pend, Wn[w]);
+            Px[w] = px_of(Wn[w]);
+            if (w > 0) Py[w - 1] = py_of(Wn[w - 1], Wn[w]);
+        }
+        for (int v = 0; v < NV; ++v) vload(j0 - 1 + v, vX[v], vY[v]);
+        issue_cell(R, isrc, kx, j0 + 2, pend);
+        T Un[4] = {T(0), T(0), T(0), T(0)};
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        T my_rate = T(0);
+        const bool stage_mode = a.mode == MODE_STAGE;
+        const bool combine = stage_mode && a.alpha != T(0);
+
+        for (int j = j0; j <= j1; ++j) {
+            // U^n of row j (combined at iteration j+1), issued early
+            T Un_next[4] = {T(0), T(0), T(0), T(0)};
+            if (combine && out_lane && j < j1) {
+                const int x = j * R.pitch + i;
+                for (int k = 0; k < 4; ++k) Un_next[k] = R.un[x + k * R.plane];
+            }
+
+            // ---- the two faces of this lane: west x-face of row j (cells lane-1 | lane) and
+            //      the y-face between rows j-1 and j (window H-1 | H)
+            Face<T> fx, fy;
+            fx.A = shup_c(Wn[H], 1, !MUSCL);
+            fx.B = Wn[H];
+            fy.A = Wn[H - 1];
+            fy.B = Wn[H];
+            if constexpr (MUSCL) {
+                fx.Am = shup_c(Wn[H], 2, false);
+                fx.Bp = shdn_c(Wn[H], 1);
+                fy.Am = Wn[H - 2];
+                fy.Bp = Wn[H + 1];
             } else {
-                const int ff = f - TL::NFX;
-                fa = ff % TX; fb = ff / TX;
-                inside = (i0 + fa < ni) && (j0 + fb <= nj);
-                Ax = fa + H; Ay = fb - 1 + H; dxs = 0; dys = 1;
-                if (CURV) {
-                    Sx = -(S.vy[fb + 1][fa + 2] - S.vy[fb + 1][fa + 1]);
-                    Sy = dx + (S.vx[fb + 1][fa + 2] - S.vx[fb + 1][fa + 1]);
-                } else { Sx = T(0); Sy = dx; }
+                fx.Am = fx.Bp = fx.A;
+                fy.Am = fy.Bp = fy.A;
             }
-            T F[4] = {T(0), T(0), T(0), T(0)};
-            const uint8_t fA = S.flag[Ay][Ax], fB = S.flag[Ay + dys][Ax + dxs];
-            if (inside && !((fA & fB) & 1)) {
-                const T len = sqrt(Sx * Sx + Sy * Sy);
-                const T nx = Sx / len, ny = Sy / len;
-                T WL[4], WR[4];
-                for (int k = 0; k < 4; ++k) { WL[k] = S.W[k][Ay][Ax]; WR[k] = S.W[k][Ay + dys][Ax + dxs]; }
-                if ((fA | fB) != 0) {
-                    // Wall face: the first-order fluid state and its mirror image about this face.
-                    if (fA) { for (int k = 0; k < 4; ++k) WL[k] = WR[k]; mirror_vel(WL[1], WL[2], nx, ny); }
-                    else { for (int k = 0; k < 4; ++k) WR[k] = WL[k]; mirror_vel(WR[1], WR[2], nx, ny); }
-                } else if (MUSCL) {
-                    T Am[4], Bp[4];
-                    for (int k = 0; k < 4; ++k) {
-                        Am[k] = S.W[k][Ay - dys][Ax - dxs];
-                        Bp[k] = S.W[k][Ay + 2 * dys][Ax + 2 * dxs];
-                    }
-                    if (S.flag[Ay - dys][Ax - dxs] & 1) {   // solid stencil cell: mirror of A about their face
-                        T tx, ty;
-                        if (isx) {
-                            if (CURV) { tx = dy + (S.vy[fb + 2][fa] - S.vy[fb + 1][fa]); ty = -(S.vx[fb + 2][fa] - S.vx[fb + 1][fa]); }
-                            else { tx = dy; ty = T(0); }
-                        } else {
-                            if (CURV) { tx = -(S.vy[fb][fa + 2] - S.vy[fb][fa + 1]); ty = dx + (S.vx[fb][fa + 2] - S.vx[fb][fa + 1]); }
-                            else { tx = T(0); ty = dx; }
-                        }
-                        const T l = sqrt(tx * tx + ty * ty);
-                        for (int k = 0; k < 4; ++k) Am[k] = WL[k];
-                        mirror_vel(Am[1], Am[2], tx / l, ty / l);
-                    }
-                    if (S.flag[Ay + 2 * dys][Ax + 2 * dxs] & 1) {
-                        T tx, ty;
-                        if (isx) {
-                            if (CURV) { tx = dy + (S.vy[fb + 2][fa + 2] - S.vy[fb + 1][fa + 2]); ty = -(S.vx[fb + 2][fa + 2] - S.vx[fb + 1][fa + 2]); }
-                            else { tx = dy; ty = T(0); }
-                        } else {
-                            if (CURV) { tx = -(S.vy[fb + 2][fa + 2] - S.vy[fb + 2][fa + 1]); ty = dx + (S.vx[fb + 2][fa + 2] - S.vx[fb + 2][fa + 1]); }
-                            else { tx = T(0); ty = dx; }
-                        }
-                        const T l = sqrt(tx * tx + ty * ty);
-                        for (int k = 0; k < 4; ++k) Bp[k] = WR[k];
-                        mirror_vel(Bp[1], Bp[2], tx / l, ty / l);
-                    }
-                    T rL[4], rR[4], lLs[4], lRs[4];
-                    const bool vl = G.limiter == 2;
-                    for (int k = 0; k < 4; ++k) {
-                        const T d0 = WL[k] - Am[k], d1 = WR[k] - WL[k], d2 = Bp[k] - WR[k];
-                        T lL, lR;
-                        if (vl) {
-                            lL = (d0 * d1 <= T(0)) ? T(0) : (d0 * tabs(d1) + tabs(d0) * d1) / (tabs(d0) + tabs(d1));
-                            lR = (d1 * d2 <= T(0)) ? T(0) : (d1 * tabs(d2) + tabs(d1) * d2) / (tabs(d1) + tabs(d2));
-                        } else {
-                            lL = T(0.5) * (sgn(d0) + sgn(d1)) * tmin(tabs(d0), tabs(d1));
-                            lR = T(0.5) * (sgn(d1) + sgn(d2)) * tmin(tabs(d1), tabs(d2));
-                        }
-                        lLs[k] = lL;
-                        lRs[k] = lR;
-                        rL[k] = WL[k] + T(0.5) * lL;
-                        rR[k] = WR[k] - T(0.5) * lR;
-                    }
-                    // Positivity of the reconstructed density and pressure, else first order. In
-                    // FP32 a value within rounding of zero is re-decided exactly in FP64.
-                    bool pos = rL[0] > T(0) && rL[3] > T(0) && rR[0] > T(0) && rR[3] > T(0);
-                    if (sizeof(T) == 4 && pos) {
-                        const T eps = T(1e-6);
-                        if (rL[0] < eps * WL[0] || rL[3] < eps * WL[3] || rR[0] < eps * WR[0] || rR[3] < eps * WR[3]) {
-                            pos = ((double)WL[0] + 0.5 * (double)lLs[0] > 0.0) && ((double)WL[3] + 0.5 * (double)lLs[3] > 0.0) &&
-                                  ((double)WR[0] - 0.5 * (double)lRs[0] > 0.0) && ((double)WR[3] - 0.5 * (double)lRs[3] > 0.0);
-                        }
-                    }
-                    if (pos) for (int k = 0; k < 4; ++k) { WL[k] = rL[k]; WR[k] = rR[k]; }
+            if (use_s1) {
+                // Eq. 96 in 2D: the face and the transverse faces of both cells.
+                const T pym_l = shup(Py[H - 1], 1), pyp_l = shup(Py[H], 1);
+                const T pxm_r = shdn(Px[H - 1], 1), px0_r = shdn(Px[H], 1);
+                T ax = vmin(vmin(Px[H], pym_l), vmin(vmin(pyp_l, Py[H - 1]), Py[H]));
+                T ay = vmin(vmin(Py[H - 1], Px[H - 1]), vmin(vmin(pxm_r, Px[H]), px0_r));
+                if constexpr (PACKED) {
+                    const V2 s1 = detector_of(mk2(ax, ay));
+                    fx.s1 = s1.v.x; fy.s1 = s1.v.y;
+                } else {
+                    fx.s1 = detector_of(ax); fy.s1 = detector_of(ay);
                 }
-                T s1 = T(1);
-                if (G.use_s1) {
-                    T am;
-                    if (isx) {   // face column fa, row fb: cells A = (fa-1, fb), B = (fa, fb)
-                        am = tmin(tmin(S.Px[fb + 1][fa], S.Py[fb][fa]), tmin(S.Py[fb + 1][fa], S.Py[fb][fa + 1]));
-                        am = tmin(am, S.Py[fb + 1][fa + 1]);
-                    } else {     // face row fb, column fa: cells A = (fa, fb-1), B = (fa, fb)
-                        am = tmin(tmin(S.Py[fb][fa + 1], S.Px[fb][fa]), tmin(S.Px[fb][fa + 1], S.Px[fb + 1][fa]));
-                        am = tmin(am, S.Px[fb + 1][fa + 1]);
-                    }
-                    s1 = pow8(fmach(am));
-                }
-                const Side<T> sl = make_side(WL[0], WL[1], WL[2], WL[3], nx, ny, K);
-                const Side<T> sr = make_side(WR[0], WR[1], WR[2], WR[3], nx, ny, K);
-                roeam_flux(sl, sr, nx, ny, s1, K, F);
-                for (int k = 0; k < 4; ++k) F[k] *= len;
-            }
-            if (isx) { for (int k = 0; k < 4; ++k) S.Fx[k][fb][fa] = F[k]; }
-            else { for (int k = 0; k < 4; ++k) S.Fy[k][fb][fa] = F[k]; }
-        }
-        __syncthreads();
-
-        // ---- 4. residual, stage combination, next-step rate, status
-        double dt = 0.0;
-        if (a.mode == MODE_STAGE)
-            dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / __longlong_as_double((long long)a.rate_rd[g]);
-        const T tdt = T(dt);
-        double my_rate = 0.0;
-        for (int cidx = tid; cidx < TX * TY; cidx += NT) {
-            const int ca = cidx % TX, cb = cidx / TX;
-            const int i = i0 + ca, j = j0 + cb;
-            if (i >= ni || j >= nj) continue;
-            const bool solid = has_solid && (S.flag[cb + H][ca + H] & 1);
-            CellGeom<T> cg;
-            if (CURV) {
-                cg = cell_geom(S.vx[cb + 1][ca + 1], S.vx[cb + 1][ca + 2], S.vx[cb + 2][ca + 1], S.vx[cb + 2][ca + 2],
-                               S.vy[cb + 1][ca + 1], S.vy[cb + 1][ca + 2], S.vy[cb + 2][ca + 1], S.vy[cb + 2][ca + 2],
-                               dx, dy);
             } else {
-                cg.Xx = dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = dx; cg.V = dx * dy;
+                fx.s1 = fy.s1 = T(1);
             }
-            T R[4];
-            for (int k = 0; k < 4; ++k)
-                R[k] = solid ? T(0)
-                             : ((S.Fx[k][cb][ca] - S.Fx[k][cb][ca + 1]) + (S.Fy[k][cb][ca] - S.Fy[k][cb + 1][ca])) / cg.V;
-            const long long c = G.off + (long long)j * G.pitch + i;
-            if (a.mode == MODE_STAGE) {
-                T out[4];
-                for (int k = 0; k < 4; ++k) {
-                    const T upd = a.src[c + k * G.plane] + tdt * R[k];
-                    out[k] = (a.alpha == T(0)) ? a.beta * upd : a.alpha * a.un[c + k * G.plane] + a.beta * upd;
+            if constexpr (CURV) {
+                // x-face: vertices (i, j), (i, j+1); y-face: vertices (i, j), (i+1, j)
+                T sx = K.dy + (vY[2] - vY[1]), sy = -(vX[2] - vX[1]);
+                fx.len = sqrt(sx * sx + sy * sy);
+                T li = T(1) / fx.len;
+                fx.nx = sx * li; fx.ny = sy * li;
+                const T xr = shdn(vX[1], 1), yr = shdn(vY[1], 1);
+                sx = -(yr - vY[1]); sy = K.dx + (xr - vX[1]);
+                fy.len = sqrt(sx * sx + sy * sy);
+                li = T(1) / fy.len;
+                fy.nx = sx * li; fy.ny = sy * li;
+                if constexpr (MUSCL) {
+                    // normals of the faces Am|A and B|Bp of both faces (mirrors at solid cells)
+                    fx.nAmx = shup(fx.nx, 1); fx.nAmy = shup(fx.ny, 1);
+                    fx.nBpx = shdn(fx.nx, 1); fx.nBpy = shdn(fx.ny, 1);
+                    const T x0 = shdn(vX[0], 1), y0 = shdn(vY[0], 1), x3 = shdn(vX[3], 1), y3 = shdn(vY[3], 1);
+                    T tx = -(y0 - vY[0]), ty = K.dx + (x0 - vX[0]), l = T(1) / sqrt(tx * tx + ty * ty);
+                    fy.nAmx = tx * l; fy.nAmy = ty * l;
+                    tx = -(y3 - vY[3]); ty = K.dx + (x3 - vX[3]); l = T(1) / sqrt(tx * tx + ty * ty);
+                    fy.nBpx = tx * l; fy.nBpy = ty * l;
+                } else {
+                    fx.nAmx = fx.nBpx = fx.nx; fx.nAmy = fx.nBpy = fx.ny;
+                    fy.nAmx = fy.nBpx = fy.nx; fy.nAmy = fy.nBpy = fy.ny;
                 }
-                for (int k = 0; k < 4; ++k) a.dst[c + k * G.plane] = out[k];
-                if (!solid) {
-                    const T u = out[1] / out[0], v = out[2] / out[0];
-                    const T p = K.gm1 * (out[3] - T(0.5) * out[0] * (u * u + v * v));
-                    if (!(out[0] > T(0)) || !(p > T(0))) {
-                        const bool fin = isfinite((double)out[0]) && isfinite((double)p);
-                        atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
-                    } else if (a.want_rate) {
-                        my_rate = fmax(my_rate, (double)cell_rate(out[0], u, v, p, cg, K));
+            } else {
+                fx.nx = T(1); fx.ny = T(0); fx.len = K.dy;
+                fy.nx = T(0); fy.ny = T(1); fy.len = K.dx;
+                fx.nAmx = fx.nBpx = T(1); fx.nAmy = fx.nBpy = T(0);
+                fy.nAmx = fy.nBpx = T(0); fy.nAmy = fy.nBpy = T(1);
+            }
+
+            T Fw[4], Fs[4];
+            // walls, solid cells (and FP64) take the scalar path; batches without walls or solid
+            // cells never do in FP32
+            bool scalar = !PACKED;
+            if constexpr (PACKED && WALLS)
+                scalar = __any_sync(0xffffffffu, face_is_wall(fx, MUSCL) || face_is_wall(fy, MUSCL));
+            if constexpr (PACKED && MUSCL) {
+                // an FP32 reconstruction within rounding of zero is decided in FP64 (scalar path)
+                if (!scalar) {
+                    const T eps = T(1e-5);
+                    const bool marginal =
+                        (fx.A.r < eps * fx.B.r) || (fx.B.r < eps * fx.A.r) || (fx.A.p < eps * fx.B.p) ||
+                        (fx.B.p < eps * fx.A.p) || (fy.A.r < eps * fy.B.r) || (fy.B.r < eps * fy.A.r) ||
+                        (fy.A.p < eps * fy.B.p) || (fy.B.p < eps * fy.A.p) || (fx.Am.p < eps * fx.A.p) ||
+                        (fx.Bp.p < eps * fx.B.p) || (fy.Am.p < eps * fy.A.p) || (fy.Bp.p < eps * fy.B.p) ||
+                        (fx.Am.r < eps * fx.A.r) || (fx.Bp.r < eps * fx.B.r) || (fy.Am.r < eps * fy.A.r) ||
+                        (fy.Bp.r < eps * fy.B.r);
+                    scalar = __any_sync(0xffffffffu, marginal);
+                }
+            }
+            if (scalar) {
+                if constexpr (!PACKED || WALLS || MUSCL) {
+                    face_scalar<T, MUSCL>(fx, K, eps1, xi_form, vanleer, Fw);
+                    face_scalar<T, MUSCL>(fy, K, eps1, xi_form, vanleer, Fs);
+                }
+            } else if constexpr (PACKED) {
+                faces_packed<MUSCL, CURV>(fx, fy, K, eps1, xi_form, vanleer, Fw, Fs);
+            }
+            if (!(i >= 0 && i <= ni && j < nj)) { Fw[0] = Fw[1] = Fw[2] = Fw[3] = T(0); }
+            if (!(icol && j <= nj)) { Fs[0] = Fs[1] = Fs[2] = Fs[3] = T(0); }
+
+            // ---- finish row j-1: R = (acc - F_north) / V, then the stage combination
+            if (j > j0) {
+                CellGeom<T> cg;
+                if constexpr (CURV) {
+                    const T x00 = vX[0], y00 = vY[0], x01 = vX[1], y01 = vY[1];
+                    const T x10 = shdn(x00, 1), y10 = shdn(y00, 1), x11 = shdn(x01, 1), y11 = shdn(y01, 1);
+                    cg = cell_geom(x00, x10, x01, x11, y00, y10, y01, y11, K.dx, K.dy);
+                } else {
+                    cg.Xx = K.dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = K.dx; cg.V = K.V;
+                }
+                if (out_lane) {
+                    const bool solid = WALLS && (Wn[H - 1].fl & 1);
+                    const T Vi = CURV ? T(1) / cg.V : K.Vi;
+                    T Rs[4];
+                    for (int k = 0; k < 4; ++k) Rs[k] = solid ? T(0) : (acc[k] - Fs[k]) * Vi;
+                    const int x = (j - 1) * R.pitch + i;
+                    if (stage_mode) {
+                        T out[4];
+                        for (int k = 0; k < 4; ++k) {
+                            // U^(k) of this cell, loaded two iterations ago (an L1 hit)
+                            const T upd = __ldg(R.src + x + k * R.plane) + dt * Rs[k];
+                            out[k] = combine ? a.alpha * Un[k] + a.beta * upd : upd;
+                        }
+                        for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = out[k];
+                        if (!solid) {
+                            const T ri = rcp(out[0]);
+                            const T uu = out[1] * ri, vv = out[2] * ri;
+                            const T p = K.gm1 * (out[3] - T(0.5) * out[0] * (uu * uu + vv * vv));
+                            if (!(out[0] > T(0)) || !(p > T(0))) {
+                                const bool fin = isfinite((double)out[0]) && isfinite((double)p);
+                                atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
+                            } else if (a.want_rate) {
+                                my_rate = vmax(my_rate, cell_rate<CURV>(out[0], uu, vv, p, cg, K));
+                            }
+                        }
+                    } else if (a.mode == MODE_RESIDUAL) {
+                        for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = Rs[k];
+                    } else if (!solid) {
+                        for (int k = 0; k < 4; ++k) {
+                            const double rk = (double)Rs[k];
+                            acc_s[k] += rk * rk;
+                            acc_m[k] = fmax(acc_m[k], fabs(rk));
+                        }
                     }
                 }
-            } else if (a.mode == MODE_RESIDUAL) {
-                for (int k = 0; k < 4; ++k) a.dst[c + k * G.plane] = R[k];
-            } else if (!solid) {
-                for (int k = 0; k < 4; ++k) {
-                    const double rk = (double)R[k];
-                    acc_s[k] += rk * rk;
-                    acc_m[k] = fmax(acc_m[k], fabs(rk));
-                }
+            }
+            if (j == j1) break;
+            for (int k = 0; k < 4; ++k) Un[k] = Un_next[k];
+            for (int k = 0; k < 4; ++k) acc[k] = Fw[k] - shdn(Fw[k], 1) + Fs[k];
+
+            // ---- advance the window: row j+2 enters from the prefetch
+            for (int w = 0; w < NW - 1; ++w) { Wn[w] = Wn[w + 1]; Px[w] = Px[w + 1]; }
+            for (int w = 0; w < NW - 2; ++w) Py[w] = Py[w + 1];
+            finish_cell<T, MUSCL, CURV, WALLS>(R, K, i, isrc, kx, j + 2, pend, Wn[NW - 1]);
+            Px[NW - 1] = px_of(Wn[NW - 1]);
+            Py[NW - 2] = py_of(Wn[NW - 2], Wn[NW - 1]);
+            issue_cell(R, isrc, kx, j + 3, pend);
+            if constexpr (CURV) {
+                for (int v = 0; v < NV - 1; ++v) { vX[v] = vX[v + 1]; vY[v] = vY[v + 1]; }
+                vload(j + 3, vX[NV - 1], vY[NV - 1]);
             }
         }
         if (a.want_rate) {
-            const double m = block_max<NT>(my_rate, red);
-            if (tid == 0 && m > 0.0) atomicMax(a.rate_wr + g, rate_bits(m));
+            for (int o = 16; o > 0; o >>= 1) my_rate = vmax(my_rate, __shfl_xor_sync(0xffffffffu, my_rate, o));
+            if (lane == 0 && my_rate > T(0)) atomicMax(a.rate_wr + g, rate_bits(my_rate));
         }
     }
 
@@ -572,31 +832,46 @@ __global__ void __launch_bounds__(NT) stage_kernel(const StageArgs<T> a)
                 const double x = __shfl_xor_sync(0xffffffffu, v[k], o);
                 v[k] = k < 4 ? v[k] + x : fmax(v[k], x);
             }
+        if (lane == 0)
+            for (int k = 0; k < 8; ++k) wred[threadIdx.x >> 5][k] = v[k];
         __syncthreads();
-        if ((tid & 31) == 0)
-            for (int k = 0; k < 8; ++k) wred[tid >> 5][k] = v[k];
-        __syncthreads();
-        if (tid < 8) {
-            double r = tid < 4 ? 0.0 : 0.0;
-            for (int w = 0; w < NT / 32; ++w) r = tid < 4 ? r + wred[w][tid] : fmax(r, wred[w][tid]);
-            a.partials[(size_t)blockIdx.x * 8 + tid] = r;
+        if (threadIdx.x < 8) {
+            double r = 0.0;
+            for (int w = 0; w < NT / 32; ++w) r = threadIdx.x < 4 ? r + wred[w][threadIdx.x] : fmax(r, wred[w][threadIdx.x]);
+            a.partials[(size_t)blockIdx.x * 8 + threadIdx.x] = r;
         }
     }
+}
+
+// Block-wide max of a non-negative value (all threads must call); valid in thread 0.
+template <int NT, typename T> __device__ __forceinline__ T block_max(T v, T *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = vmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    T r = T(0);
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < NT / 32 ? red[threadIdx.x] : T(0);
+        for (int o = 16; o > 0; o >>= 1) r = vmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    }
+    return r;
 }
 
 // ------------------------------------------------------------------ small kernels
 // Largest rate of every fluid cell of grids [g_lo, g_hi) (blockIdx.y = grid).
 template <typename T, bool CURV>
-__global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, int g_lo, const T *U, const T *vdx,
-                                                   const T *vdy, const uint8_t *solid, unsigned long long *rate)
+__global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, const GridCoef<T> *coef, int g_lo, const T *U,
+                                                   const T *vdx, const T *vdy, const uint8_t *solid,
+                                                   unsigned long long *rate)
 {
-    __shared__ double red[8];
+    __shared__ T red[8];
     const int g = g_lo + blockIdx.y;
     const GridDev &G = grids[g];
-    const Coef<T> K = make_coef<T>(G);
-    const T dx = T(G.dx), dy = T(G.dy);
+    const GridCoef<T> K = coef[g];
     const long long n = (long long)G.ni * G.nj;
-    double m = 0.0;
+    T m = T(0);
     for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
         const int i = (int)(q % G.ni), j = (int)(q / G.ni);
         if (G.soff >= 0 && solid[G.soff + q]) continue;
@@ -607,14 +882,14 @@ __global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, int g_l
         if (CURV) {
             const long long b = G.voff + (long long)j * G.vpitch + i;
             cg = cell_geom(vdx[b], vdx[b + 1], vdx[b + G.vpitch], vdx[b + G.vpitch + 1], vdy[b], vdy[b + 1],
-                           vdy[b + G.vpitch], vdy[b + G.vpitch + 1], dx, dy);
+                           vdy[b + G.vpitch], vdy[b + G.vpitch + 1], K.dx, K.dy);
         } else {
-            cg.Xx = dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = dx; cg.V = dx * dy;
+            cg.Xx = K.dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = K.dx; cg.V = K.V;
         }
-        m = fmax(m, (double)cell_rate(r, u, v, p, cg, K));
+        m = vmax(m, cell_rate<CURV>(r, u, v, p, cg, K));
     }
     m = block_max<256>(m, red);
-    if (threadIdx.x == 0 && m > 0.0) atomicMax(rate + g, rate_bits(m));
+    if (threadIdx.x == 0 && m > T(0)) atomicMax(rate + g, rate_bits(m));
 }
 
 template <typename T>
@@ -643,11 +918,13 @@ __global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g
 
 // FP64 block partials of sum V Q over the fluid cells of grid g (4 doubles per block).
 template <typename T, bool CURV>
-__global__ void __launch_bounds__(256) totals_kernel(const GridDev *grids, int g, const T *U, const T *vdx,
-                                                     const T *vdy, const uint8_t *solid, double *partials)
+__global__ void __launch_bounds__(256) totals_kernel(const GridDev *grids, const GridCoef<T> *coef, int g, const T *U,
+                                                     const T *vdx, const T *vdy, const uint8_t *solid,
+                                                     double *partials)
 {
     __shared__ double wred[8][4];
     const GridDev &G = grids[g];
+    const GridCoef<T> K = coef[g];
     const long long n = (long long)G.ni * G.nj;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
@@ -657,7 +934,7 @@ __global__ void __launch_bounds__(256) totals_kernel(const GridDev *grids, int g
         if (CURV) {
             const long long b = G.voff + (long long)j * G.vpitch + i;
             V = (double)cell_geom(vdx[b], vdx[b + 1], vdx[b + G.vpitch], vdx[b + G.vpitch + 1], vdy[b], vdy[b + 1],
-                                  vdy[b + G.vpitch], vdy[b + G.vpitch + 1], T(G.dx), T(G.dy)).V;
+                                  vdy[b + G.vpitch], vdy[b + G.vpitch + 1], K.dx, K.dy).V;
         } else {
             V = G.dx * G.dy;
         }
@@ -677,31 +954,17 @@ __global__ void __launch_bounds__(256) totals_kernel(const GridDev *grids, int g
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, int CFG, bool MUSCL, bool CURV> struct StageVariant {
-    static constexpr int TX = TILE_CFGS[CFG].tx, TY = TILE_CFGS[CFG].ty, NT = TILE_CFGS[CFG].nt;
-    static constexpr size_t SMEM = tile_smem_bytes<T, TX, TY, MUSCL, CURV>();
-    // Opts the kernel in to its dynamic shared-memory size (once per process; the handle
-    // calls occupancy() at creation, before any launch or graph capture).
-    static cudaError_t prepare()
-    {
-        static cudaError_t done = cudaErrorNotReady;
-        if (done != cudaSuccess)
-            done = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NT, MUSCL, CURV>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-        return done;
-    }
+template <typename T, bool MUSCL, bool CURV, bool WALLS> struct StageVariant {
+    static constexpr int NT = STAGE_THREADS;
     static cudaError_t launch(const StageArgs<T> &a, int nblocks, cudaStream_t s)
     {
-        cudaError_t e = prepare();
-        if (e != cudaSuccess) return e;
-        stage_kernel<T, TX, TY, NT, MUSCL, CURV><<<nblocks, NT, SMEM, s>>>(a);
+        stage_kernel<T, MUSCL, CURV, WALLS, NT><<<nblocks, NT, 0, s>>>(a);
         return cudaGetLastError();
     }
     static int occupancy()
     {
-        if (prepare() != cudaSuccess) return 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T, TX, TY, NT, MUSCL, CURV>, NT, SMEM) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T, MUSCL, CURV, WALLS, NT>, NT, 0) !=
             cudaSuccess)
             return 1;
         return n > 0 ? n : 1;
@@ -709,48 +972,41 @@ template <typename T, int CFG, bool MUSCL, bool CURV> struct StageVariant {
 };
 
 template <typename T, bool MUSCL, bool CURV>
-static cudaError_t stage_dispatch_cfg(const StageArgs<T> &a, int cfg, int nblocks, cudaStream_t s)
+static cudaError_t stage_walls(const StageArgs<T> &a, int walls, int nblocks, cudaStream_t s)
 {
-    switch (cfg) {
-    case 0: return StageVariant<T, 0, MUSCL, CURV>::launch(a, nblocks, s);
-    case 1: return StageVariant<T, 1, MUSCL, CURV>::launch(a, nblocks, s);
-    default: return StageVariant<T, 2, MUSCL, CURV>::launch(a, nblocks, s);
-    }
+    return walls ? StageVariant<T, MUSCL, CURV, true>::launch(a, nblocks, s)
+                 : StageVariant<T, MUSCL, CURV, false>::launch(a, nblocks, s);
 }
-
 template <typename T, bool MUSCL, bool CURV>
-static int stage_occ_cfg(int cfg)
+static int occ_walls(int walls)
 {
-    switch (cfg) {
-    case 0: return StageVariant<T, 0, MUSCL, CURV>::occupancy();
-    case 1: return StageVariant<T, 1, MUSCL, CURV>::occupancy();
-    default: return StageVariant<T, 2, MUSCL, CURV>::occupancy();
-    }
+    return walls ? StageVariant<T, MUSCL, CURV, true>::occupancy() : StageVariant<T, MUSCL, CURV, false>::occupancy();
 }
 
 template <typename T>
-cudaError_t Launchers<T>::stage(const StageArgs<T> &a, int muscl, int curv, int cfg, int nblocks, cudaStream_t s)
+cudaError_t Launchers<T>::stage(const StageArgs<T> &a, int muscl, int curv, int walls, int nblocks, cudaStream_t s)
 {
     if (a.tile_hi <= a.tile_lo) return cudaSuccess;
-    if (muscl) return curv ? stage_dispatch_cfg<T, true, true>(a, cfg, nblocks, s) : stage_dispatch_cfg<T, true, false>(a, cfg, nblocks, s);
-    return curv ? stage_dispatch_cfg<T, false, true>(a, cfg, nblocks, s) : stage_dispatch_cfg<T, false, false>(a, cfg, nblocks, s);
+    if (muscl) return curv ? stage_walls<T, true, true>(a, walls, nblocks, s) : stage_walls<T, true, false>(a, walls, nblocks, s);
+    return curv ? stage_walls<T, false, true>(a, walls, nblocks, s) : stage_walls<T, false, false>(a, walls, nblocks, s);
 }
 
 template <typename T>
-int Launchers<T>::stage_occupancy(int muscl, int curv, int cfg)
+int Launchers<T>::stage_occupancy(int muscl, int curv, int walls)
 {
-    if (muscl) return curv ? stage_occ_cfg<T, true, true>(cfg) : stage_occ_cfg<T, true, false>(cfg);
-    return curv ? stage_occ_cfg<T, false, true>(cfg) : stage_occ_cfg<T, false, false>(cfg);
+    if (muscl) return curv ? occ_walls<T, true, true>(walls) : occ_walls<T, true, false>(walls);
+    return curv ? occ_walls<T, false, true>(walls) : occ_walls<T, false, false>(walls);
 }
 
 template <typename T>
-cudaError_t Launchers<T>::rate(const GridDev *grids, int g_lo, int g_hi, const T *U, const T *vdx, const T *vdy,
-                               const uint8_t *solid, unsigned long long *rate, int curv, cudaStream_t s)
+cudaError_t Launchers<T>::rate(const GridDev *grids, const GridCoef<T> *coef, int g_lo, int g_hi, const T *U,
+                               const T *vdx, const T *vdy, const uint8_t *solid, unsigned long long *rate, int curv,
+                               cudaStream_t s)
 {
     if (g_hi <= g_lo) return cudaSuccess;
     dim3 grid(64, g_hi - g_lo);
-    if (curv) rate_kernel<T, true><<<grid, 256, 0, s>>>(grids, g_lo, U, vdx, vdy, solid, rate);
-    else rate_kernel<T, false><<<grid, 256, 0, s>>>(grids, g_lo, U, vdx, vdy, solid, rate);
+    if (curv) rate_kernel<T, true><<<grid, 256, 0, s>>>(grids, coef, g_lo, U, vdx, vdy, solid, rate);
+    else rate_kernel<T, false><<<grid, 256, 0, s>>>(grids, coef, g_lo, U, vdx, vdy, solid, rate);
     return cudaGetLastError();
 }
 
@@ -777,11 +1033,12 @@ cudaError_t Launchers<T>::unpack(const GridDev *grids, int g_lo, int g_hi, int m
 }
 
 template <typename T>
-cudaError_t Launchers<T>::totals(const GridDev *grids, int g, const T *U, const T *vdx, const T *vdy,
-                                 const uint8_t *solid, double *partials, int nblocks, int curv, cudaStream_t s)
+cudaError_t Launchers<T>::totals(const GridDev *grids, const GridCoef<T> *coef, int g, const T *U, const T *vdx,
+                                 const T *vdy, const uint8_t *solid, double *partials, int nblocks, int curv,
+                                 cudaStream_t s)
 {
-    if (curv) totals_kernel<T, true><<<nblocks, 256, 0, s>>>(grids, g, U, vdx, vdy, solid, partials);
-    else totals_kernel<T, false><<<nblocks, 256, 0, s>>>(grids, g, U, vdx, vdy, solid, partials);
+    if (curv) totals_kernel<T, true><<<nblocks, 256, 0, s>>>(grids, coef, g, U, vdx, vdy, solid, partials);
+    else totals_kernel<T, false><<<nblocks, 256, 0, s>>>(grids, coef, g, U, vdx, vdy, solid, partials);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,8 @@ ROEAM_NORM_L2, ROEAM_NORM_LINF = 0, 1
 # Entry points declared in include/roeam.h (checked by the tests).
 EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual",
            "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
-           "roeam_cell_count", "roeam_last_error", "roeam_version"]
+           "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
+           "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune"]
 
 
 class RoeamError(RuntimeError):
@@ -74,8 +75,13 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_cell_count.restype = C.c_longlong
     lib.roeam_last_error.restype = C.c_char_p
     lib.roeam_version.restype = C.c_int
+    lib.roeam_tile_config_count.restype = C.c_int
+    lib.roeam_tile_config_info.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.roeam_set_tile_config.argtypes = [vp, C.c_int]
+    lib.roeam_autotune.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
     for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
-                 "roeam_residual_norm", "roeam_conserved_totals", "roeam_check"):
+                 "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
+                 "roeam_set_tile_config", "roeam_autotune"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -149,6 +155,30 @@ def roeam_cell_count(h: int, grid_idx: int = -1) -> int:
 
 def roeam_version() -> int:
     return int(load_library().roeam_version())
+
+
+def roeam_tile_config_count() -> int:
+    return int(load_library().roeam_tile_config_count())
+
+
+def roeam_tile_config_info(cfg: int):
+    tx, ty, nt = C.c_int(), C.c_int(), C.c_int()
+    _check(load_library().roeam_tile_config_info(cfg, C.byref(tx), C.byref(ty), C.byref(nt)))
+    return tx.value, ty.value, nt.value
+
+
+def roeam_set_tile_config(h: int, cfg: int) -> None:
+    _check(load_library().roeam_set_tile_config(C.c_void_p(h), cfg))
+
+
+def roeam_autotune(h: int, cfl: float = 0.5, steps: int = 3):
+    """Returns (best tile config, ms per step of every config)."""
+    n = roeam_tile_config_count()
+    ms = np.zeros(n)
+    best = C.c_int()
+    _check(load_library().roeam_autotune(C.c_void_p(h), cfl, steps, C.byref(best),
+                                         ms.ctypes.data_as(C.POINTER(C.c_double))))
+    return best.value, ms
 
 
 # ----------------------------------------------------------------------------- convenience
@@ -252,6 +282,12 @@ class Batch:
 
     def check(self):
         roeam_check(self.handle)
+
+    def set_tile_config(self, cfg: int):
+        roeam_set_tile_config(self.handle, cfg)
+
+    def autotune(self, cfl: float = 0.5, steps: int = 3):
+        return roeam_autotune(self.handle, cfl, steps)
 
     @property
     def launches(self) -> int:
