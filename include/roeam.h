@@ -136,6 +136,19 @@ roeam_status roeam_conserved_totals(roeam_grid *g, int grid_idx, double out[4]);
  * (ROEAM_E_NONPOSITIVE / ROEAM_E_NONFINITE), clearing it; ROEAM_OK if none. */
 roeam_status roeam_check(roeam_grid *g);
 
+/* Residual of one grid, like roeam_flux_residual (res_out non-null, grid_idx >= 0), for
+ * callers that cannot allocate device memory when they need it: a host that runs this
+ * library inside a fixed device-memory budget with no allocation after start-up, or a
+ * monitor next to a solver whose memory pool owns the device. The paper has no counterpart;
+ * it is a service of this library. The call allocates nothing: its scratch is a fixed
+ * 24 MiB array that every GPU loading the library holds until the process exits. A grid
+ * fits if 4 x nj x pitch working-precision values (pitch = ni rounded up to 32) plus
+ * 4 x ni x nj doubles fit in it (about 512 x 512 cells); larger grids get ROEAM_E_ARG with
+ * a message saying so. The first call on a device looks the array up (once per device);
+ * make that first call before any stream capture. Calls share the array: calls whose work
+ * overlaps on the GPU race. Synchronises. */
+roeam_status roeam_flux_residual_noalloc(roeam_grid *g, int grid_idx, double *res_out);
+
 /* Number of tile shapes (stage-kernel variants) the library is built with. */
 int roeam_tile_config_count(void);
 

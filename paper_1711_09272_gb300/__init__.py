@@ -8,4 +8,4 @@ from .roeam import (Batch, RoeamError, load_library, make_desc, roeam_cell_count
                     roeam_conserved_totals, roeam_create_grid, roeam_destroy_grid, roeam_flux_residual,
                     roeam_get_state, roeam_launch_count, roeam_residual_norm, roeam_rk_step, roeam_set_state,
                     roeam_version, roeam_tile_config_count, roeam_tile_config_info, roeam_set_tile_config,
-                    roeam_autotune, EXPORTS, LIB_PATH, ROEAM_NORM_L2, ROEAM_NORM_LINF)
+                    roeam_autotune, roeam_flux_residual_noalloc, EXPORTS, LIB_PATH, ROEAM_NORM_L2, ROEAM_NORM_LINF)

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -783,3 +784,92 @@ long long roeam_cell_count(const roeam_grid *g, int grid_idx)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Residual without device allocation.
+//
+// Some callers cannot allocate device memory when they need a residual: a host that hands
+// the GPU to this library inside a fixed memory budget and forbids allocation after
+// start-up, or a monitor that runs next to a solver whose memory pool owns the whole
+// device. roeam_flux_residual_noalloc serves them. Its scratch (the residual in working
+// precision and its float64 copy) lives in the fixed-size array below, which every GPU that
+// loads this library holds until the process exits. Every call shares that array and
+// leaves its contents behind; all of it that a call reads is written by the same call
+// first, so nothing has to start at zero. Calls whose kernels overlap on the GPU (other
+// streams, other threads) race on the array.
+namespace {
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(24) << 20;   // 24 MiB
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[256] = {nullptr};
+}  // namespace
+
+static __device__ __align__(256) unsigned char roeam_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of the scratch array on `device` (which must be current). The first call on
+// a device looks it up with cudaGetSymbolAddress; host code may not use the array's name as
+// an address.
+roeam_status noalloc_scratch(int device, void **out)
+{
+    if (device < 0 || device >= 256) return fail(ROEAM_E_ARG, "device %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, roeam_noalloc_scratch);
+        if (e != cudaSuccess)
+            return fail(ROEAM_E_CUDA, "cudaGetSymbolAddress(roeam_noalloc_scratch): %s", cudaGetErrorString(e));
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status do_residual_noalloc(roeam_grid *g, int idx, double *out)
+{
+    const GridDev &G = g->hg[idx];
+    const size_t bytes_t = (sizeof(T) * 4 * (size_t)G.plane + 255) / 256 * 256;
+    const size_t bytes_d = sizeof(double) * 4 * (size_t)G.ni * G.nj;
+    if (bytes_t + bytes_d > NOALLOC_SCRATCH_BYTES)
+        return fail(ROEAM_E_ARG,
+                    "grid %d (%d x %d cells) needs %zu bytes of scratch; the allocation-free residual holds %zu "
+                    "(about 512 x 512 cells)",
+                    idx, G.ni, G.nj, bytes_t + bytes_d, NOALLOC_SCRATCH_BYTES);
+    void *scratch = nullptr;
+    roeam_status st = noalloc_scratch(g->device, &scratch);
+    if (st != ROEAM_OK) return st;
+    // The kernels address this grid at element offsets G.off (working-precision planes) and
+    // G.poff (float64 copy); shift the bases so that both land at the start of their regions.
+    const uintptr_t base_t = (uintptr_t)scratch - sizeof(T) * (uintptr_t)G.off;
+    const uintptr_t region_d = (uintptr_t)scratch + bytes_t;
+    const uintptr_t base_d = region_d - sizeof(double) * (uintptr_t)G.poff;
+    StageArgs<T> a = base_args<T>(g);
+    a.mode = MODE_RESIDUAL;
+    a.src = (const T *)g->U;
+    a.un = (const T *)g->U;
+    a.dst = (T *)base_t;
+    a.units = g->d_units_grid;
+    a.tile_lo = g->h_tile_base[idx];
+    a.tile_hi = g->h_tile_base[idx + 1];
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, g->stream));
+    CUDA_TRY(Launchers<T>::unpack(g->d_grids, idx, idx + 1, G.ni * G.nj, (const T *)base_t, (double *)base_d,
+                                  g->stream));
+    g->launches += 2;
+    CUDA_TRY(cudaMemcpyAsync(out, (const void *)region_d, bytes_d, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return ROEAM_OK;
+}
+
+}  // namespace
+
+extern "C" roeam_status roeam_flux_residual_noalloc(roeam_grid *g, int grid_idx, double *res_out)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    if (grid_idx < 0 || grid_idx >= g->count) return fail(ROEAM_E_ARG, "grid_idx %d out of range [0, %d)", grid_idx, g->count);
+    if (!res_out) return fail(ROEAM_E_ARG, "res_out must be non-null");
+    if (!g->state_set[grid_idx]) return fail(ROEAM_E_STATE, "state of grid %d not set", grid_idx);
+    CUDA_TRY(cudaSetDevice(g->device));
+    return g->precision == 32 ? do_residual_noalloc<float>(g, grid_idx, res_out)
+                              : do_residual_noalloc<double>(g, grid_idx, res_out);
+}

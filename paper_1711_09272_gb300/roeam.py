@@ -25,7 +25,7 @@ ROEAM_NORM_L2, ROEAM_NORM_LINF = 0, 1
 EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual",
            "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
            "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
-           "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune"]
+           "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc"]
 
 
 class RoeamError(RuntimeError):
@@ -79,9 +79,10 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_tile_config_info.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.roeam_set_tile_config.argtypes = [vp, C.c_int]
     lib.roeam_autotune.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
+    lib.roeam_flux_residual_noalloc.argtypes = [vp, C.c_int, vp]
     for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
-                 "roeam_set_tile_config", "roeam_autotune"):
+                 "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -122,6 +123,12 @@ def roeam_get_state(h: int, grid_idx: int, out) -> None:
 
 def roeam_flux_residual(h: int, grid_idx: int, out=None) -> None:
     _check(load_library().roeam_flux_residual(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(out) if out is not None else None)))
+
+
+def roeam_flux_residual_noalloc(h: int, grid_idx: int, out) -> None:
+    """Residual of one grid into `out` without any device allocation by the library (its
+    scratch is a fixed array in the library; see include/roeam.h)."""
+    _check(load_library().roeam_flux_residual_noalloc(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(out))))
 
 
 def roeam_rk_step(h: int, cfl: float, dt_fixed: float, nsteps: int, dt_last=None) -> None:
