@@ -65,7 +65,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.reader = threading.Thread(target=self._read, daemon=True)
             self.reader.start()
@@ -107,6 +107,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("paper_1711_09272_gb300/csrc/roeam_kernels.cuh", "paper_1711_09272_gb300/csrc/roeam_internal.h")
+
+
+def kernel_hash() -> str:
+    """Hash of the stage kernel's sources; ncu traffic figures are only reported for the kernel
+    version they were measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(ncells: int):
+    """DRAM bytes per stage-kernel launch from the committed ncu summary, scaled to this launch
+    size, or None when the summary belongs to another kernel version."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d["dram_bytes_per_cell_per_launch"] * ncells
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -141,12 +169,14 @@ def run_reference(args):
     total_cells = 0
     times = []
     ncores = 1
+    # each step: one SSP-RK3 step of consecutive grids of the batch for a bounded time, sized so
+    # that the whole run stays within about two minutes
+    budget = max(0.05, min(2.0, 120.0 / (args.steps + args.warmup)))
     for it in range(args.warmup + args.steps):
-        # one step = one SSP-RK3 step of a bounded sample of the batch (about 2 s of CPU work)
         t0 = time.perf_counter()
         cells = 0
         k = (it * 5) % len(specs)
-        while time.perf_counter() - t0 < 2.0:
+        while time.perf_counter() - t0 < budget:
             s, U = specs[k], states[k]
             oracle.OracleGrid(s).step(U, cfl=0.5)
             cells += s.ncells * 3
@@ -160,9 +190,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "each step: consecutive grids of the batch for ~2 s, one step each"},
+        "config": {"workload": WORKLOAD,
+                   "sample": f"each step: consecutive grids of the batch for {budget:.2f} s, one SSP-RK3 step each"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                         "sample": "FP64 C oracle, single thread, consecutive grids of the batch for ~2 s per step"},
+                         "sample": f"FP64 C oracle, single thread, consecutive grids of the batch, {budget:.2f} s per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -179,13 +210,17 @@ def run_ours(args):
     import paper_1711_09272_gb300 as P
 
     prec = 32
-    specs, states = W.batch(512, seed=W.DEFAULT_SEED + rank, recon=W.RECON_FIRST)
+    specs, states = W.batch(args.grids, seed=W.DEFAULT_SEED + rank, recon=W.RECON_FIRST)
     ncells = sum(s.ncells for s in specs)
     stream = torch.cuda.current_stream()
     b = P.Batch(specs, precision=prec, device=local, cuda_stream=stream.cuda_stream)
     packed = np.concatenate([U.ravel() for U in states])
     b.set_state(packed, -1)
 
+    tuned = None
+    if not args.no_autotune:
+        best, ms = b.autotune(0.5, 3)   # picks the work-unit shape; restores the state
+        tuned = {"chosen": int(best), "ms_per_step": [round(float(x), 4) for x in ms]}
     # warm-up (also captures the graph of this (cfl, dt) pair)
     for _ in range(args.warmup):
         b.step(cfl=0.5, nsteps=1)
@@ -232,35 +267,35 @@ def run_ours(args):
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with pinned host buffers
-    h_in = torch.from_numpy(packed).pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
-    e2e_steps = max(2, min(args.steps, 5))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        P.roeam_set_state(b.handle, -1, h_in)
-        b.step(cfl=0.5, nsteps=1)
-        P.roeam_get_state(b.handle, -1, h_out)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = ncells * 3 / e2e_s / 1e9
-    nbytes = packed.nbytes
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(packed).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        e2e_steps = 5
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            P.roeam_set_state(b.handle, -1, h_in)
+            b.step(cfl=0.5, nsteps=1)
+            P.roeam_get_state(b.handle, -1, h_out)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": ncells * 3 / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": packed.nbytes,
+               "d2h_bytes_per_step": packed.nbytes,
+               "path": "roeam_set_state(pinned fp64) + roeam_rk_step(1) + roeam_get_state(pinned fp64)"}
 
     line = None
     if rank == 0:
         cpu_v, cpu_sample = (None, None)
         if world == 1 and not args.no_cpu:
             cpu_v, cpu_sample = cpu_baseline(specs, states, steps=1, budget_s=args.cpu_budget)
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tpath):
-            with open(tpath) as f:
-                traffic = json.load(f).get("stage_fp32_first_batch512_bytes_per_launch")
+        traffic = measured_traffic(ncells)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grids_per_gpu": len(specs), "cells_per_gpu": ncells,
-                       "recon": "first order", "cfl": 0.5,
+            "config": {"workload": WORKLOAD if args.grids == 512 else WORKLOAD.replace("512", str(args.grids), 1),
+                       "grids_per_gpu": len(specs), "cells_per_gpu": ncells,
+                       "recon": "first order", "cfl": 0.5, "autotune": tuned,
                        "l2": "inputs larger than L2 (3 state buffers of %.0f MB each)" % (16 * ncells / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -268,8 +303,7 @@ def run_ours(args):
                          "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec], "launch_ms": launch_ms},
             "cpu_baseline": None if cpu_v is None else {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                                         "sample": cpu_sample},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                    "path": "roeam_set_state(pinned fp64) + roeam_rk_step(1) + roeam_get_state(pinned fp64)"},
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
@@ -283,11 +317,14 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--grids", type=int, default=512, help="grids in the batch (512 is the benchmark workload)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default work-unit shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
