@@ -142,6 +142,28 @@ def dist_info():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Every rank advances its own independent batch (weak scaling): seed of rank r."""
+    return W.DEFAULT_SEED + rank
+
+
+def reduce_max(value: float, world: int, device: str = "cuda") -> float:
+    """Max over ranks of a per-rank time (the only collective of the benchmark)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(cells_per_rank: int, world: int, steps: int, ms: float) -> float:
+    """Whole-job Gcell-updates per second per RK stage: all ranks' cells x 3 stages x steps
+    over the slowest rank's time."""
+    return cells_per_rank * world * 3 * steps / (ms * 1e-3) / 1e9
+
+
 def cpu_baseline(specs, states, steps: int = 1, budget_s: float = 20.0):
     """Times the FP64 C oracle (single thread, as it stands) on the first grids of the batch
     until `budget_s` is reached; returns (Gcell-updates/s per stage, sample description)."""
@@ -210,7 +232,7 @@ def run_ours(args):
     import paper_1711_09272_gb300 as P
 
     prec = 32
-    specs, states = W.batch(args.grids, seed=W.DEFAULT_SEED + rank, recon=W.RECON_FIRST)
+    specs, states = W.batch(args.grids, seed=rank_seed(rank), recon=W.RECON_FIRST)
     ncells = sum(s.ncells for s in specs)
     stream = torch.cuda.current_stream()
     b = P.Batch(specs, precision=prec, device=local, cuda_stream=stream.cuda_stream)
@@ -245,12 +267,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     launches = b.launches - l0
     b.check()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    total_cells = ncells * world
-    value = total_cells * 3 * args.steps / (ms * 1e-3) / 1e9
+    ms = reduce_max(ms, world)
+    value = weak_value(ncells, world, args.steps, ms)
 
     # ---- per-launch duration of the stage kernel (events around single steps = 3 launches)
     per = []

@@ -211,49 +211,65 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     F[3] = F3c - vfma(xi, QR3 - QL3, vfma(dUu, QR3 + QL3, A * Hh));
 }
 
-// Largest dissipative signal speed normal to a face: |U| + max(c, c~/theta), Eqs. 99-101 on
-// the cell state (classical |U| + c when theta = 1).
-template <typename T> __device__ __forceinline__ T signal_speed(T Un, T c, T q2, T mr2)
-{
-    const T th = vmin(vmax(mr2, q2 / (c * c)), T(1));
-    if (th >= T(1)) return vabs(Un) + c;
-    const T om = T(1) - th;
-    const T ct = T(0.5) * sqrt(T(4) * c * c * th + om * om * Un * Un);
-    return vabs(Un) + vmax(c, ct / th);
-}
-
 // ------------------------------------------------------------------ geometry
 // Vertex (I, J) of a curvilinear grid sits at (I dx + dX(I, J), J dy + dY(I, J)).
 // x-face on vertex column I, row J: S = (dy + dY(I,J+1) - dY(I,J), -(dX(I,J+1) - dX(I,J))).
 // y-face on vertex row J, column I: S = (-(dY(I+1,J) - dY(I,J)), dx + dX(I+1,J) - dX(I,J)).
 template <typename T> struct CellGeom { T Xx, Xy, Yx, Yy, V; };
 
+// Arithmetic with explicit rounding (no FMA contraction), so that the time-step rate of a
+// state comes out bit-identical wherever it is evaluated (the stage-3 epilogue and the rate
+// kernel after a restart from a saved state).
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T rsub(T a, T b) { return radd(a, -b); }
+
 template <typename T>
 __device__ __forceinline__ CellGeom<T> cell_geom(T x00, T x10, T x01, T x11, T y00, T y10, T y01, T y11, T dx, T dy)
 {
+    const T h = T(0.5);
     CellGeom<T> c;
-    c.Xx = dy + T(0.5) * ((y01 - y00) + (y11 - y10));
-    c.Xy = -T(0.5) * ((x01 - x00) + (x11 - x10));
-    c.Yx = -T(0.5) * ((y10 - y00) + (y11 - y01));
-    c.Yy = dx + T(0.5) * ((x10 - x00) + (x11 - x01));
-    const T d1x = dx + (x11 - x00), d1y = dy + (y11 - y00);
-    const T d2x = -dx + (x01 - x10), d2y = dy + (y01 - y10);
-    c.V = T(0.5) * (d1x * d2y - d1y * d2x);
+    c.Xx = radd(dy, rmul(h, radd(rsub(y01, y00), rsub(y11, y10))));
+    c.Xy = -rmul(h, radd(rsub(x01, x00), rsub(x11, x10)));
+    c.Yx = -rmul(h, radd(rsub(y10, y00), rsub(y11, y01)));
+    c.Yy = radd(dx, rmul(h, radd(rsub(x10, x00), rsub(x11, x01))));
+    const T d1x = radd(dx, rsub(x11, x00)), d1y = radd(dy, rsub(y11, y00));
+    const T d2x = radd(-dx, rsub(x01, x10)), d2y = radd(dy, rsub(y01, y10));
+    c.V = rmul(h, rsub(rmul(d1x, d2y), rmul(d1y, d2x)));
     return c;
 }
 
-template <bool CURV, typename T>
-__device__ __forceinline__ T cell_rate(T r, T u, T v, T p, const CellGeom<T> &cg, const GridCoef<T> &K)
+// Largest dissipative signal speed normal to a face: |U| + max(c, c~/theta), Eqs. 99-101 on
+// the cell state (classical |U| + c when theta = 1).
+template <typename T> __device__ __forceinline__ T signal_speed(T Un, T c, T q2, T mr2)
 {
-    const T c = sqrt(K.g * p / r);
-    const T q2 = u * u + v * v;
+    const T c2 = rmul(c, c);
+    const T th = vmin(vmax(mr2, q2 / c2), T(1));
+    if (th >= T(1)) return radd(vabs(Un), c);
+    const T om = rsub(T(1), th);
+    const T ct = rmul(T(0.5), sqrt(radd(rmul(rmul(T(4), c2), th), rmul(rmul(om, om), rmul(Un, Un)))));
+    return radd(vabs(Un), vmax(c, ct / th));
+}
+
+// The rate sum_dir speed_dir |S_dir| / V of one cell, from its conserved state.
+template <bool CURV, typename T>
+__device__ __forceinline__ T cell_rate_cons(T r, T ru, T rv, T rE, const CellGeom<T> &cg, const GridCoef<T> &K)
+{
+    const T ri = T(1) / r;
+    const T u = rmul(ru, ri), v = rmul(rv, ri);
+    const T q2 = radd(rmul(u, u), rmul(v, v));
+    const T p = rmul(K.gm1, rsub(rE, rmul(rmul(T(0.5), r), q2)));
+    const T c = sqrt(rmul(rmul(K.g, p), ri));
     if constexpr (CURV) {
-        const T lx = sqrt(cg.Xx * cg.Xx + cg.Xy * cg.Xy), ly = sqrt(cg.Yx * cg.Yx + cg.Yy * cg.Yy);
-        const T sx = signal_speed((u * cg.Xx + v * cg.Xy) / lx, c, q2, K.mr2);
-        const T sy = signal_speed((u * cg.Yx + v * cg.Yy) / ly, c, q2, K.mr2);
-        return (sx * lx + sy * ly) / cg.V;
+        const T lx = sqrt(radd(rmul(cg.Xx, cg.Xx), rmul(cg.Xy, cg.Xy)));
+        const T ly = sqrt(radd(rmul(cg.Yx, cg.Yx), rmul(cg.Yy, cg.Yy)));
+        const T sx = signal_speed(radd(rmul(u, cg.Xx), rmul(v, cg.Xy)) / lx, c, q2, K.mr2);
+        const T sy = signal_speed(radd(rmul(u, cg.Yx), rmul(v, cg.Yy)) / ly, c, q2, K.mr2);
+        return radd(rmul(sx, lx), rmul(sy, ly)) / cg.V;
     } else {
-        return signal_speed(u, c, q2, K.mr2) / K.dx + signal_speed(v, c, q2, K.mr2) / K.dy;
+        return radd(signal_speed(u, c, q2, K.mr2) / K.dx, signal_speed(v, c, q2, K.mr2) / K.dy);
     }
 }
 
@@ -786,7 +802,7 @@ __global__ void __launch_bounds__(NT, STAGE_MIN_BLOCKS) stage_kernel(const Stage
                                 const bool fin = isfinite((double)out[0]) && isfinite((double)p);
                                 atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
                             } else if (a.want_rate) {
-                                my_rate = vmax(my_rate, cell_rate<CURV>(out[0], uu, vv, p, cg, K));
+                                my_rate = vmax(my_rate, cell_rate_cons<CURV>(out[0], out[1], out[2], out[3], cg, K));
                             }
                         }
                     } else if (a.mode == MODE_RESIDUAL) {
@@ -876,8 +892,6 @@ __global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, const G
         const int i = (int)(q % G.ni), j = (int)(q / G.ni);
         if (G.soff >= 0 && solid[G.soff + q]) continue;
         const long long c = G.off + (long long)j * G.pitch + i;
-        const T r = U[c], u = U[c + G.plane] / r, v = U[c + 2 * G.plane] / r;
-        const T p = K.gm1 * (U[c + 3 * G.plane] - T(0.5) * r * (u * u + v * v));
         CellGeom<T> cg;
         if (CURV) {
             const long long b = G.voff + (long long)j * G.vpitch + i;
@@ -886,7 +900,7 @@ __global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, const G
         } else {
             cg.Xx = K.dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = K.dx; cg.V = K.V;
         }
-        m = vmax(m, cell_rate<CURV>(r, u, v, p, cg, K));
+        m = vmax(m, cell_rate_cons<CURV>(U[c], U[c + G.plane], U[c + 2 * G.plane], U[c + 3 * G.plane], cg, K));
     }
     m = block_max<256>(m, red);
     if (threadIdx.x == 0 && m > T(0)) atomicMax(rate + g, rate_bits(m));

@@ -1,0 +1,196 @@
+"""GPU checks of the benchmark workloads at their full sizes and of the paper's test cases.
+
+Full-size parity: after a run on the GPU, single cells of the next step are recomputed by
+the FP64 oracle on a window around them (radius 8 > the 3 stages x 2-cell stencil reach, so
+the window's own edges cannot reach the centre), with the GPU's dt and from the GPU's
+(rounded) state. Physics: the qualitative results the paper reports, on the GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from riemann_exact import sample
+
+pytestmark = pytest.mark.gpu
+
+RADIUS = 8
+
+
+def P():
+    import paper_1711_09272_gb300 as pkg
+    return pkg
+
+
+def state_scale(U):
+    m = np.sqrt(U[1] ** 2 + U[2] ** 2).max()
+    return np.array([np.abs(U[0]).max(), m, m, np.abs(U[3]).max()])
+
+
+def window(spec, U, ci, cj, R=RADIUS):
+    """Sub-grid of `spec` around cell (ci, cj): periodic directions wrap, domain sides keep
+    their boundary condition, cut sides are zero-gradient (too far to matter)."""
+    def axis(c, n, lo_bc, hi_bc):
+        if lo_bc == W.PERIODIC:
+            idx = np.arange(c - R, c + R + 1) % n
+            return idx, W.OUTFLOW, W.OUTFLOW, R
+        a, b = max(0, c - R), min(n, c + R + 1)
+        return np.arange(a, b), (lo_bc if a == 0 else W.OUTFLOW), (hi_bc if b == n else W.OUTFLOW), c - a
+    ii, bw, be, oi = axis(ci, spec.ni, spec.bc[0], spec.bc[1])
+    jj, bs, bn, oj = axis(cj, spec.nj, spec.bc[2], spec.bc[3])
+    sub = W.GridSpec(ni=len(ii), nj=len(jj), dx=spec.dx, dy=spec.dy, bc=(bw, be, bs, bn), inflow=spec.inflow,
+                     params=spec.params)
+    if spec.xv is not None:
+        assert spec.bc[0] != W.PERIODIC and spec.bc[2] != W.PERIODIC
+        vi = np.arange(ii[0], ii[-1] + 2)
+        vj = np.arange(jj[0], jj[-1] + 2)
+        sub.xv = spec.xv[np.ix_(vj, vi)]
+        sub.yv = spec.yv[np.ix_(vj, vi)]
+    if spec.solid is not None:
+        sub.solid = spec.solid[np.ix_(jj, ii)]
+    return sub, U[:, jj][:, :, ii], oi, oj
+
+
+def check_cells(spec, U0, U1, dt, cells, tol):
+    scale = state_scale(U0)
+    worst = 0.0
+    for ci, cj in cells:
+        sub, Uw, oi, oj = window(spec, U0, ci, cj)
+        Uo, _ = oracle.OracleGrid(sub).step(Uw, dt_fixed=dt)
+        err = np.max(np.abs(Uo[:, oj, oi] - U1[:, cj, ci]) / scale)
+        worst = max(worst, err)
+        assert err <= tol, (ci, cj, err)
+    return worst
+
+
+def test_batch_full_size_sampled_parity():
+    """The batched FP32 workload (512 grids) after 20 steps: sampled cells of step 21."""
+    specs, states = W.batch(512)
+    rng = W.SplitMix64(99)
+    with P().Batch(specs, precision=32) as b:
+        b.set_states(states)
+        b.step(0.5, nsteps=20)
+        U0 = b.get_states()
+        dts = b.step(0.5, nsteps=1, want_dt=True)
+        U1 = b.get_states()
+    for _ in range(24):
+        g = int(rng.uniform() * len(specs))
+        s = specs[g]
+        cells = [(int(rng.uniform() * s.ni), int(rng.uniform() * s.nj))]
+        check_cells(s, U0[g], U1[g], dts[g], cells, 1e-5)
+
+
+def test_warped_step_full_size_sampled_parity():
+    """The 4096 x 4096 curvilinear FP32 workload (MUSCL van Leer, solid block, walls, inflow,
+    outflow) after 30 steps: sampled interior, wall, inflow and block-corner cells."""
+    spec, U = W.warped_step(4096, 4096)
+    with P().Batch([spec], precision=32) as b:
+        b.set_state(U, 0)
+        b.step(0.5, nsteps=30)
+        U0 = b.get_state(0)
+        dt = b.step(0.5, nsteps=1, want_dt=True)[0]
+        U1 = b.get_state(0)
+    ib = int(np.argmax(spec.solid[0]))
+    jb = int(np.argmin(spec.solid[:, -1]))
+    rng = W.SplitMix64(7)
+    cells = [(ib - 1, jb), (ib - 2, jb + 1), (ib, jb), (ib + 3, jb), (ib - 1, 2), (0, 100), (1, 4000), (4095, 2000),
+             (2000, 0), (3000, 4095), (ib - 1, 0)]
+    cells += [(int(rng.uniform() * 4096), int(rng.uniform() * 4096)) for _ in range(8)]
+    cells = [(i, j) for i, j in cells if not spec.solid[j, i]]
+    check_cells(spec, U0, U1, dt, cells, 1e-5)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_checkpoint_restart_is_bit_identical(prec):
+    spec = W.with_params(W.warped_periodic(48, amp=0.15), recon=2)
+    U = W.random_smooth_state(spec, seed=8, mach=0.7, amp=0.4)
+    with P().Batch([spec], precision=prec) as a:
+        a.set_state(U, 0)
+        a.step(0.5, nsteps=10)
+        U10 = a.get_state(0)
+        a.step(0.5, nsteps=13)
+        U23 = a.get_state(0)
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U10, 0)
+        b.step(0.5, nsteps=13)
+        assert np.array_equal(b.get_state(0), U23)
+
+
+@pytest.mark.parametrize("name", ["expansion", "near_vacuum", "strong"])
+def test_shock_tubes_gpu(name):
+    """Section 7.1 shock tubes on the GPU in FP64: the trajectory follows the oracle with the
+    same time steps, converges to the exact Riemann solution, and (expansion tube) shows no
+    expansion shock."""
+    spec, U = W.shock_tube(name, 200, 4)
+    tend = W.SHOCK_TUBES[name][3]
+    ramp = name == "strong"
+    dts = []
+    with P().Batch([spec], precision=64) as b:
+        b.set_state(U, 0)
+        t, n = 0.0, 0
+        while t < tend - 1e-14:
+            cfl = min(0.4, 0.02 * 1.05 ** n) if ramp else 0.5
+            dt = b.step(cfl, nsteps=1, want_dt=True)[0]
+            if t + dt > tend:   # redo the last step with the remaining time
+                b.set_state(Ug, 0)
+                dt = tend - t
+                b.step(0.5, dt_fixed=dt, nsteps=1)
+            Ug = b.get_state(0)
+            dts.append(dt)
+            t += dt
+            n += 1
+    g = oracle.OracleGrid(spec)
+    Uo = U.copy()
+    for dt in dts:
+        Uo, _ = g.step(Uo, dt_fixed=dt)
+    assert np.max(np.abs(Ug - Uo).reshape(4, -1).max(axis=1) / state_scale(Uo)) < 1e-9
+    l, r, x0, _ = W.SHOCK_TUBES[name]
+    xc, _ = spec.cell_centres()
+    rho_ex, _, _ = sample(l, r, (xc[0] - x0) / tend)
+    assert np.mean(np.abs(Ug[0, 0] - rho_ex)) < {"expansion": 0.05, "near_vacuum": 0.05, "strong": 0.3}[name]
+    if name == "expansion":
+        assert np.max(np.abs(np.diff(Ug[0, 0]))[50:70]) < 0.15
+
+
+@pytest.mark.parametrize("eps1", [0, 1])
+def test_quirk_no_carbuncle_fp32(eps1):
+    """Section 7.2 duct at the benchmark size (800 x 20, centreline +-1e-6, FP32, CFL 0.25,
+    4000 steps): density stays positive and the planar Mach-6 shock stays planar."""
+    spec, U = W.quirk(800, 20, eps_y=1e-6, eps1=eps1)
+    with P().Batch([spec], precision=32) as b:
+        b.set_state(U, 0)
+        b.step(0.25, nsteps=4000)
+        Ug = b.get_state(0)   # raises on a non-positive or non-finite state
+    rho = Ug[0]
+    jump = W.QUIRK_POST[0] - W.QUIRK_PRE[0]
+    indicator = float(np.max(rho.max(axis=0) - rho.min(axis=0)) / jump)
+    xs = np.argmax(rho.mean(axis=0) < 0.5 * (W.QUIRK_POST[0] + W.QUIRK_PRE[0]))
+    assert 300 < xs < 790   # the shock moved about 6 x t downstream and is still inside
+    assert indicator < 1e-2, indicator
+
+
+def test_gresho_low_mach_fp64_fp32():
+    """Low-Mach workload (Gresho vortex, 256 x 256, minmod, M = 0.01, seeded 1e-3 checkerboard,
+    2000 steps): the checkerboard mode decays (delta U_p of Eq. 89), pressure stays O(M^2)
+    around p0, and FP32 tracks FP64."""
+    out = {}
+    for prec in (64, 32):
+        spec, U = W.gresho(256, mach=0.01)
+        with P().Batch([spec], precision=prec) as b:
+            b.set_state(U, 0)
+            b.step(0.5, nsteps=2000)
+            out[prec] = b.get_state(0)
+    n = 256
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    sign = np.where((ii + jj) % 2 == 0, 1.0, -1.0)
+    _, _, _, p0 = W.cons_to_prim(U)
+    _, _, _, p64 = W.cons_to_prim(out[64])
+    amp0 = abs(np.mean((p0 - p0.mean()) * sign))
+    amp1 = abs(np.mean((p64 - p64.mean()) * sign))
+    assert amp1 < 0.5 * amp0, (amp0, amp1)
+    pinf = 1.0 / (1.4 * 0.01 ** 2)
+    assert np.max(np.abs(p64 - p0)) / pinf < 1e-3
+    rel = np.max(np.abs(out[32] - out[64]).reshape(4, -1).max(axis=1) / state_scale(out[64]))
+    assert rel < 1e-4, rel
