@@ -173,8 +173,10 @@ def test_quirk_no_carbuncle_fp32(eps1):
 
 def test_gresho_low_mach_fp64_fp32():
     """Low-Mach workload (Gresho vortex, 256 x 256, minmod, M = 0.01, seeded 1e-3 checkerboard,
-    2000 steps): the checkerboard mode decays (delta U_p of Eq. 89), pressure stays O(M^2)
-    around p0, and FP32 tracks FP64."""
+    2000 steps): the checkerboard mode decays (delta U_p of Eq. 89) and pressure stays O(M^2)
+    around p0, in FP64 and in FP32. FP32 drifts from FP64 over the trajectory because its
+    pressure rounding (~6e-8 p0) is ~4e-4 of the dynamic pressure at M = 0.01; the bound on the
+    drift is loose (the per-step 1e-5 bound is checked by the parity tests)."""
     out = {}
     for prec in (64, 32):
         spec, U = W.gresho(256, mach=0.01)
@@ -186,11 +188,12 @@ def test_gresho_low_mach_fp64_fp32():
     jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     sign = np.where((ii + jj) % 2 == 0, 1.0, -1.0)
     _, _, _, p0 = W.cons_to_prim(U)
-    _, _, _, p64 = W.cons_to_prim(out[64])
     amp0 = abs(np.mean((p0 - p0.mean()) * sign))
-    amp1 = abs(np.mean((p64 - p64.mean()) * sign))
-    assert amp1 < 0.5 * amp0, (amp0, amp1)
     pinf = 1.0 / (1.4 * 0.01 ** 2)
-    assert np.max(np.abs(p64 - p0)) / pinf < 1e-3
+    for prec in (64, 32):
+        _, _, _, p = W.cons_to_prim(out[prec])
+        amp1 = abs(np.mean((p - p.mean()) * sign))
+        assert amp1 < 0.5 * amp0, (prec, amp0, amp1)
+        assert np.max(np.abs(p - p0)) / pinf < 1e-3
     rel = np.max(np.abs(out[32] - out[64]).reshape(4, -1).max(axis=1) / state_scale(out[64]))
-    assert rel < 1e-4, rel
+    assert rel < 5e-3, rel
