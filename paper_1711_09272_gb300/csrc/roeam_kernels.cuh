@@ -69,16 +69,37 @@ template <typename T> __device__ __forceinline__ T sel(bool m, T a, T b) { retur
 __device__ __forceinline__ V2 sel(B2 m, V2 a, V2 b) { return mk2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y); }
 
 // Reciprocal, reciprocal square root and square root (of a non-negative value). FP32 uses
-// the fast hardware approximations; FP64 the correctly rounded operations.
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+// the single-instruction hardware approximations (PTX rcp/rsqrt/sqrt .approx); FP64 the
+// correctly rounded operations.
+__device__ __forceinline__ float rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsq(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt0(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ V2 rcp(V2 x) { return mk2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ V2 rsq(V2 x) { return mk2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
-__device__ __forceinline__ float sqrt0(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt0(double x) { return sqrt(x); }
-__device__ __forceinline__ V2 sqrt0(V2 x) { return mk2(sqrtf(x.v.x), sqrtf(x.v.y)); }
+__device__ __forceinline__ V2 rcp(V2 x) { return mk2(rcp(x.v.x), rcp(x.v.y)); }
+__device__ __forceinline__ V2 rsq(V2 x) { return mk2(rsq(x.v.x), rsq(x.v.y)); }
+__device__ __forceinline__ V2 sqrt0(V2 x) { return mk2(sqrt0(x.v.x), sqrt0(x.v.y)); }
+
+// copysign(a, b): magnitude of a, sign of b.
+__device__ __forceinline__ float vcopysign(float a, float b) { return copysignf(a, b); }
+__device__ __forceinline__ double vcopysign(double a, double b) { return copysign(a, b); }
+__device__ __forceinline__ V2 vcopysign(V2 a, V2 b) { return mk2(copysignf(a.v.x, b.v.x), copysignf(a.v.y, b.v.y)); }
 
 // sgn with sgn(0) = 0.
 template <typename V> __device__ __forceinline__ V sgnv(V a)
@@ -191,8 +212,10 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
         xi = vmax(xi, (one - fMb8) * fM8 * vmin(splat<V>(K.eps2) * ch, frr));
     }
 
+    // sgn(U) min(|U|', c): min(|U|', c) = 0 whenever U = 0 (then |U|' = 0), so the sign can
+    // be copied onto it
     const V mn = vmin(Up, ch);
-    const V smc = sgnv(uh) * mn * chi;
+    const V smc = vcopysign(mn, uh) * chi;
     const V pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmax(ch - Up, zero) * rh * du);
     const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
     const V om = one - th;
@@ -200,7 +223,8 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     const V rX = rsq(X);           // 1 / (2 c~)
     const V ct = half * X * rX;    // c~
     const V Ut = half * (one + th) * uh;
-    const V term = vfma(om, Up - uh * rX * sgnv(Ut) * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
+    // U sgn(U~) min(|U~|, c~) = |U| min(|U~|, c~): U~ = (1 + theta) U / 2 has the sign of U
+    const V term = vfma(om, Up - aU * rX * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
     const V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
     const V dUu = half * smc * du;
 
@@ -565,21 +589,21 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
     derive<T, MUSCL>(c, K);
 }
 
-template <typename T> __device__ __forceinline__ WC<T> shup_c(const WC<T> &c, int d, bool derived)
+template <bool WALLS, typename T> __device__ __forceinline__ WC<T> shup_c(const WC<T> &c, int d, bool derived)
 {
     WC<T> o;
     o.r = shup(c.r, d); o.u = shup(c.u, d); o.v = shup(c.v, d); o.p = shup(c.p, d);
     if (derived) { o.c2 = shup(c.c2, d); o.H = shup(c.H, d); o.sr = shup(c.sr, d); o.Mq = shup(c.Mq, d); }
     else { o.c2 = o.H = o.sr = o.Mq = T(0); }
-    o.fl = (uint8_t)__shfl_up_sync(0xffffffffu, (int)c.fl, d);
+    o.fl = WALLS ? (uint8_t)__shfl_up_sync(0xffffffffu, (int)c.fl, d) : (uint8_t)0;
     return o;
 }
-template <typename T> __device__ __forceinline__ WC<T> shdn_c(const WC<T> &c, int d)
+template <bool WALLS, typename T> __device__ __forceinline__ WC<T> shdn_c(const WC<T> &c, int d)
 {
     WC<T> o;
     o.r = shdn(c.r, d); o.u = shdn(c.u, d); o.v = shdn(c.v, d); o.p = shdn(c.p, d);
     o.c2 = o.H = o.sr = o.Mq = T(0);
-    o.fl = (uint8_t)__shfl_down_sync(0xffffffffu, (int)c.fl, d);
+    o.fl = WALLS ? (uint8_t)__shfl_down_sync(0xffffffffu, (int)c.fl, d) : (uint8_t)0;
     return o;
 }
 
@@ -680,13 +704,13 @@ __global__ void __launch_bounds__(NT, STAGE_MIN_BLOCKS) stage_kernel(const Stage
             // ---- the two faces of this lane: west x-face of row j (cells lane-1 | lane) and
             //      the y-face between rows j-1 and j (window H-1 | H)
             Face<T> fx, fy;
-            fx.A = shup_c(Wn[H], 1, !MUSCL);
+            fx.A = shup_c<WALLS>(Wn[H], 1, !MUSCL);
             fx.B = Wn[H];
             fy.A = Wn[H - 1];
             fy.B = Wn[H];
             if constexpr (MUSCL) {
-                fx.Am = shup_c(Wn[H], 2, false);
-                fx.Bp = shdn_c(Wn[H], 1);
+                fx.Am = shup_c<WALLS>(Wn[H], 2, false);
+                fx.Bp = shdn_c<WALLS>(Wn[H], 1);
                 fy.Am = Wn[H - 2];
                 fy.Bp = Wn[H + 1];
             } else {
