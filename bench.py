@@ -181,6 +181,52 @@ def cpu_baseline(specs, states, steps: int = 1, budget_s: float = 20.0):
     return cells / t_total / 1e9, f"first {used} of {len(specs)} grids of the same batch, {steps} SSP-RK3 step(s) each"
 
 
+def time_single(P, torch, spec, U, prec, steps, cfl=0.5, dt_fixed=0.0, warmup=3):
+    """Device time of `steps` steps of one grid; returns (ms per step, final state)."""
+    stream = torch.cuda.current_stream()
+    with P.Batch([spec], precision=prec, cuda_stream=stream.cuda_stream) as b:
+        b.set_state(U, 0)
+        b.step(cfl, dt_fixed=dt_fixed, nsteps=warmup)
+        b.set_state(U, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(cfl, dt_fixed=dt_fixed, nsteps=steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, b.get_state(0)
+
+
+def precision_comparison(P, torch, n=1024, t_end=1.0):
+    """FP32 vs FP64 on one grid at the same discretisation (isentropic vortex, first order,
+    identical fixed time steps): speed and L2 density error against the exact solution."""
+    spec, U = W.isentropic_vortex(n)
+    with P.Batch([spec], precision=64) as b:
+        b.set_state(U, 0)
+        dt0 = b.step(0.5, nsteps=1, want_dt=True)[0]
+    steps = int(np.ceil(t_end / dt0))
+    dt = t_end / steps
+    _, Ue = W.isentropic_vortex(n, t=t_end)
+    out = {"workload": f"isentropic vortex {n}x{n} periodic, first order, t = {t_end}, {steps} steps of dt = {dt:.3e}"}
+    for prec in (32, 64):
+        ms, Uf = time_single(P, torch, spec, U, prec, steps, dt_fixed=dt)
+        out[f"fp{prec}"] = {"gcell_updates_per_s_per_stage": spec.ncells * 3 / (ms * 1e-3) / 1e9,
+                            "ms_per_step": ms, "l2_rho_error": float(np.sqrt(np.mean((Uf[0] - Ue[0]) ** 2)))}
+    return out
+
+
+def warped_step_speed(P, torch, steps=20):
+    """The large curvilinear FP32 workload (4096 x 4096 warped grid, Mach-3 step, MUSCL van
+    Leer, solid block): device speed and its HBM fraction (50.67 algorithmic B/cell/stage)."""
+    spec, U = W.warped_step(4096, 4096)
+    ms, _ = time_single(P, torch, spec, U, 32, steps)
+    v = spec.ncells * 3 / (ms * 1e-3) / 1e9
+    peak, kind = peaks()
+    return {"workload": "warped step 4096x4096 FP32, MUSCL van Leer, solid block, walls/inflow/outflow",
+            "gcell_updates_per_s_per_stage": v, "ms_per_step": ms,
+            "hbm_frac": v * (128.0 / 3 + 8) / peak, "peak_gbs": peak, "peak_kind": kind}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -325,6 +371,9 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
+        if world == 1 and not args.no_extra:
+            line["precision_comparison"] = precision_comparison(P, torch)
+            line["curvilinear"] = warped_step_speed(P, torch)
         print(json.dumps(line), flush=True)
     b.close()
     if world > 1:
@@ -343,6 +392,7 @@ def main():
     ap.add_argument("--grids", type=int, default=512, help="grids in the batch (512 is the benchmark workload)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work-unit shape")
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP32/FP64 and curvilinear side measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
