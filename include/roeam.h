@@ -95,7 +95,7 @@ typedef struct {
     roeam_params p;
 } roeam_grid_desc;
 
-/* Creates a batch handle of `count` grids on CUDA device `device`, ordering its work on
+/* Creates a batch handle of `count` (1..65535) grids on CUDA device `device`, ordering its work on
  * `cuda_stream` (a cudaStream_t, or NULL). Copies every descriptor array. The state is
  * zero until roeam_set_state. On success *out receives the handle. */
 roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int device, void *cuda_stream,

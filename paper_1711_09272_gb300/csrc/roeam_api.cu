@@ -46,6 +46,7 @@ roeam_status fail(roeam_status st, const char *fmt, ...)
 long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
 
 constexpr int GRAPH_STEPS = 8;   // SSP-RK3 steps per captured graph (an even number)
+constexpr size_t MAX_GRAPHS = 8; // captured graphs kept per handle (one per (cfl, dt_fixed) pair)
 
 struct GraphKey {
     double cfl, dt_fixed;
@@ -263,6 +264,12 @@ roeam_status rk_steps(roeam_grid *g, double cfl, double dt_fixed, int nsteps)
     if (left >= GRAPH_STEPS) {
         GraphKey key{cfl, dt_fixed};
         auto it = g->graphs.find(key);
+        if (it == g->graphs.end() && g->graphs.size() >= MAX_GRAPHS) {
+            // keep the cache small: a caller that varies dt_fixed call by call rebuilds graphs
+            CUDA_TRY(cudaStreamSynchronize(g->stream));
+            for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+            g->graphs.clear();
+        }
         if (it == g->graphs.end()) {
             cudaGraph_t graph;
             CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -400,6 +407,7 @@ roeam_status do_totals(roeam_grid *g, int idx, double out[4])
 roeam_status validate(int count, const roeam_grid_desc *d)
 {
     if (count < 1 || !d) return fail(ROEAM_E_ARG, "count must be >= 1 and descs non-null");
+    if (count > 65535) return fail(ROEAM_E_ARG, "count must be <= 65535 grids per handle");
     for (int k = 0; k < count; ++k) {
         const roeam_grid_desc &q = d[k];
         const roeam_params &p = q.p;

@@ -791,8 +791,8 @@ __global__ void __launch_bounds__(NT, STAGE_MIN_BLOCKS) stage_kernel(const Stage
             } else if constexpr (PACKED) {
                 faces_packed<MUSCL, CURV>(fx, fy, K, eps1, xi_form, vanleer, Fw, Fs);
             }
-            if (!(i >= 0 && i <= ni && j < nj)) { Fw[0] = Fw[1] = Fw[2] = Fw[3] = T(0); }
-            if (!(icol && j <= nj)) { Fs[0] = Fs[1] = Fs[2] = Fs[3] = T(0); }
+            // (faces of lanes or rows outside the grid are computed from clamped or ghost states
+            //  and never reach a written cell: a written cell's faces all lie in the grid)
 
             // ---- finish row j-1: R = (acc - F_north) / V, then the stage combination
             if (j > j0) {
