@@ -68,10 +68,27 @@ struct StageArgs {
 
 // Work-unit shapes of the stage kernel: a warp sweeps a strip tx = 32 lanes wide (2H of
 // them halo) over ty rows; nt threads per CTA. The autotuner picks among these.
-constexpr int STAGE_THREADS = 128;
-#ifndef STAGE_MIN_BLOCKS
-#define STAGE_MIN_BLOCKS 3
+// One warp per CTA: registers are then allocated warp by warp, so every 8 registers saved
+// per thread buys another resident warp.
+#ifndef STAGE_THREADS_DEF
+#define STAGE_THREADS_DEF 32
 #endif
+constexpr int STAGE_THREADS = STAGE_THREADS_DEF;
+// Resident CTAs per SM the compiler is asked to fit (register budget): 13 keeps the FP32
+// first-order Cartesian kernel at 128 registers without spills (16 warps per SM); the
+// reconstructing and curvilinear FP32 variants stay at ~168 registers (12 warps) where they
+// do not spill; FP64 is left to the compiler.
+#ifndef STAGE_MIN_BLOCKS_FAST
+#define STAGE_MIN_BLOCKS_FAST 13
+#endif
+#ifndef STAGE_MIN_BLOCKS_OTHER
+#define STAGE_MIN_BLOCKS_OTHER 12
+#endif
+template <typename T, bool MUSCL, bool CURV>
+constexpr int stage_min_blocks()
+{
+    return sizeof(T) != 4 ? 1 : ((!MUSCL && !CURV) ? STAGE_MIN_BLOCKS_FAST : STAGE_MIN_BLOCKS_OTHER);
+}
 struct TileCfg { int tx, ty, nt; };
 constexpr int NUM_TILE_CFGS = 4;
 constexpr TileCfg TILE_CFGS[NUM_TILE_CFGS] = {{32, 32, STAGE_THREADS}, {32, 64, STAGE_THREADS},

@@ -608,7 +608,7 @@ template <bool WALLS, typename T> __device__ __forceinline__ WC<T> shdn_c(const 
 }
 
 template <typename T, bool MUSCL, bool CURV, bool WALLS, int NT>
-__global__ void __launch_bounds__(NT, STAGE_MIN_BLOCKS) stage_kernel(const StageArgs<T> a)
+__global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV>())) stage_kernel(const StageArgs<T> a)
 {
     constexpr int H = MUSCL ? 2 : 1;
     constexpr int NW = H + 2;          // window rows j-H .. j+1
