@@ -31,7 +31,8 @@ _LIBS = {}
 class OrcParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("m_ref", C.c_double), ("u_ref", C.c_double), ("eps2", C.c_double),
                 ("eps1", C.c_int), ("use_s1", C.c_int), ("recon", C.c_int), ("xi_form", C.c_int),
-                ("scheme", C.c_int), ("dup_mode", C.c_int), ("ufix", C.c_int), ("pad_", C.c_int)]
+                ("scheme", C.c_int), ("dup_mode", C.c_int), ("ufix", C.c_int), ("xi_roe", C.c_int),
+                ("harten", C.c_double)]
 
 
 class OrcGrid(C.Structure):
@@ -87,7 +88,8 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def make_params(p=None, *, scheme: int = 0, dup_mode: int = 0, ufix: int = 1, **over) -> OrcParams:
+def make_params(p=None, *, scheme: int = 0, dup_mode: int = 0, ufix: int = 1, xi_roe: int = 0, harten: float = 0.0,
+                **over) -> OrcParams:
     """Oracle parameter block from a workloads.SchemeParams (or keyword overrides)."""
     d = dict(gamma=1.4, m_ref=0.5, u_ref=1.0, eps2=0.05, eps1=0, use_s1=1, recon=0, xi_form=0)
     if p is not None:
@@ -95,7 +97,8 @@ def make_params(p=None, *, scheme: int = 0, dup_mode: int = 0, ufix: int = 1, **
                  recon=p.recon, xi_form=p.xi_form)
     d.update(over)
     return OrcParams(d["gamma"], d["m_ref"], d["u_ref"], d["eps2"], int(d["eps1"]), int(d["use_s1"]),
-                     int(d["recon"]), int(d["xi_form"]), int(scheme), int(dup_mode), int(ufix), 0)
+                     int(d["recon"]), int(d["xi_form"]), int(scheme), int(dup_mode), int(ufix), int(xi_roe),
+                     float(harten))
 
 
 class OracleGrid:

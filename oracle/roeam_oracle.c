@@ -68,10 +68,12 @@ typedef struct {
     int use_s1;    /* 1: detector of Eq. 95; 0: s1 = 1 (Eq. 110) */
     int recon;     /* 0 first order, 1 MUSCL minmod, 2 MUSCL van Leer */
     int xi_form;   /* 0: Eq. 86 with the Eq. 68 factor; 1: Eq. 86 literal */
-    int scheme;    /* 0 Roe-AM (Eqs. 85-109); 1 classical Roe (Eqs. 7, 13-17) */
-    int dup_mode;  /* Roe-AM delta U_p: 0 Eq. 89; 1 zero; 2 classical Eq. 17 (Section 7.6 variants) */
+    int scheme;    /* 0 Roe-AM (Eqs. 85-109); 1 classical Roe (Eq. 7 with Eqs. 8-12) */
+    int dup_mode;  /* Roe-AM delta U_p: 0 Eq. 89; 1 zero; 2 the Roe term max(0, c - |U|) dp / (rho c^2)
+                      as Section 7.6 writes it */
     int ufix;      /* 1 |U|' of Eq. 92; 0 |U|' = |U| (Section 7.1.1 variant) */
-    int pad_;
+    int xi_roe;    /* Roe-AM with xi = |U| of Eq. 13 instead of Eq. 86 (Section 7.2 variants) */
+    double harten; /* classical Roe: eps_lambda of the entropy fix of Eqs. 114-115 (0 = none) */
 } orc_params;
 
 typedef struct {
@@ -154,14 +156,23 @@ static void face_flux(const orc_params *P, const real WL[4], const real WR[4], r
     real hv[4] = {h.rho, h.rho * h.u, h.rho * h.v, h.rho * h.H};
 
     if (P->scheme == 1) {
-        /* Classical Roe in the scale framework: Eq. 7 with Eqs. 13-17; the energy slot
-         * uses Delta(rho E) and U in the pressure vector. */
+        /* Classical Roe in the scale framework: Eq. 7 with the eigenvalue forms Eqs. 8-12
+         * (Eqs. 13-17 when no entropy fix); Delta(rho E) in the xi term and U in the energy slot
+         * of the pressure vector. The entropy fix of Eqs. 114-115 replaces every eigenvalue
+         * below h = eps_lambda max(lambda_i) by (lambda^2 / h + h) / 2. */
         real aU = RABS_(h.U);
-        real xi = aU;                                              /* Eq. 13 */
-        real dpu = rmax(0, h.c - aU) * h.rho * dU;                /* Eq. 14 */
-        real dpp = sgn(h.U) * rmin(aU, h.c) * dp / h.c;           /* Eq. 15 */
-        real dUu = sgn(h.U) * rmin(aU, h.c) * dU / h.c;           /* Eq. 16 */
-        real dUp = rmax(0, h.c - aU) * dp / (h.rho * h.c2);       /* Eq. 17 */
+        real l1 = aU, l4 = RABS_(h.U - h.c), l5 = RABS_(h.U + h.c);
+        if (P->harten > 0) {
+            real hh = (real)P->harten * rmax(l1, rmax(l4, l5));
+            if (l1 < hh) l1 = (real)0.5 * (l1 * l1 / hh + hh);
+            if (l4 < hh) l4 = (real)0.5 * (l4 * l4 / hh + hh);
+            if (l5 < hh) l5 = (real)0.5 * (l5 * l5 / hh + hh);
+        }
+        real xi = l1;                                               /* Eq. 8 */
+        real dpu = ((l5 + l4) / 2 - l1) * h.rho * dU;               /* Eq. 9 */
+        real dpp = (l5 - l4) / 2 * dp / h.c;                        /* Eq. 10 */
+        real dUu = (l5 - l4) / 2 * dU / h.c;                        /* Eq. 11 */
+        real dUp = ((l5 + l4) / 2 - l1) * dp / (h.rho * h.c2);      /* Eq. 12 */
         real EL = WL[3] / (g - 1) + (real)0.5 * WL[0] * (WL[1] * WL[1] + WL[2] * WL[2]);
         real ER = WR[3] / (g - 1) + (real)0.5 * WR[0] * (WR[1] * WR[1] + WR[2] * WR[2]);
         real dQ[4] = {WR[0] - WL[0], QR[1] - QL[1], QR[2] - QL[2], ER - EL};
@@ -214,6 +225,7 @@ static void face_flux(const orc_params *P, const real WL[4], const real WR[4], r
         xi2 = (1 - fMb8) * fM8 * rmin(fef, frr);
     }
     real xi = rmax(xi1, xi2);
+    if (P->xi_roe) xi = aU;                                       /* Eq. 13 (Section 7.2 variant) */
 
     real mn = rmin(Up, h.c);
     real dpp = sgn(h.U) * mn * dp / h.c;                                  /* Eq. 87 */
@@ -222,7 +234,7 @@ static void face_flux(const orc_params *P, const real WL[4], const real WR[4], r
     if (P->dup_mode == 1)
         dUp = 0;
     else if (P->dup_mode == 2)
-        dUp = rmax(0, h.c - Up) * dp / (h.rho * h.c2);
+        dUp = rmax(0, h.c - aU) * dp / (h.rho * h.c2);                     /* Eq. 17 as in Section 7.6 */
     else
         dUp = s1 * (1 - fM8) *
               (rmax(0, ct - Up) + om * (Up - h.U / (2 * ct) * sgn(Ut) * rmin(RABS_(Ut), ct))) *

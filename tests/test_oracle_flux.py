@@ -43,7 +43,7 @@ def random_normals(n, seed):
 
 
 VARIANTS = [dict(), dict(eps1=1), dict(xi_form=1), dict(m_ref=1e-3), dict(m_ref=2.0), dict(scheme=1),
-            dict(dup_mode=1), dict(dup_mode=2), dict(ufix=0)]
+            dict(dup_mode=1), dict(dup_mode=2), dict(ufix=0), dict(xi_roe=1), dict(scheme=1, harten=0.2)]
 
 
 # ----------------------------------------------------------------------------- Eq. 98
@@ -252,6 +252,30 @@ def test_classical_roe_matrix_form():
         absA = (Rv @ np.diag(np.abs(lam)) @ np.linalg.inv(Rv)).real
         ref = 0.5 * (euler_flux(L[k], n[k])[0] + euler_flux(R[k], n[k])[0]) - 0.5 * absA @ (cons(R[k]) - cons(L[k]))
         assert np.max(np.abs(F[k] - ref)) <= 1e-10 * np.max(np.abs(ref)), k
+
+
+def test_harten_fix_matrix_form():
+    """The entropy fix of Eqs. 114-115 in the scale form equals the matrix form with every
+    eigenvalue magnitude below h = eps_lambda max|lambda| replaced by (lambda^2/h + h)/2, and
+    vanishes as eps_lambda -> 0."""
+    L = random_states(60, 181, mach=0.8)
+    R = random_states(60, 182, mach=0.8)
+    n = random_normals(60, 183)
+    for eps in (0.05, 0.2, 0.6):
+        F = oracle.face_flux(L, R, n, scheme=1, harten=eps)
+        h = oracle.roe_average(L, R)
+        for k in range(60):
+            A = jacobian_cs(h[k, :4], n[k])
+            lam, Rv = np.linalg.eig(A)
+            a = np.abs(lam.real)
+            hh = eps * a.max()
+            a = np.where(a < hh, 0.5 * (a * a / hh + hh), a)
+            absA = (Rv @ np.diag(a) @ np.linalg.inv(Rv)).real
+            ref = 0.5 * (euler_flux(L[k], n[k])[0] + euler_flux(R[k], n[k])[0]) - 0.5 * absA @ (cons(R[k]) - cons(L[k]))
+            assert np.max(np.abs(F[k] - ref)) <= 1e-10 * np.max(np.abs(ref)), (eps, k)
+    F0 = oracle.face_flux(L, R, n, scheme=1)
+    Ft = oracle.face_flux(L, R, n, scheme=1, harten=1e-300)
+    assert np.array_equal(F0, Ft)
 
 
 # ----------------------------------------------------------------------------- P5 positivity
