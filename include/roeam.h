@@ -64,12 +64,31 @@ enum { ROEAM_NORM_L2 = 0, ROEAM_NORM_LINF = 1 };
  *            falls back to first order).
  *   xi_form  0: xi of Eq. 86 with the [1 - f^8(Mbar)] factor of Eq. 68 on dU/2 (exact
  *            full upwinding for supersonic faces, Eq. 44); 1: Eq. 86 as printed.
- *   precision 32 (state and flux arithmetic in FP32; FP64 reductions) or 64. */
+ *   precision 32 (state and flux arithmetic in FP32; FP64 reductions) or 64.
+ *
+ * Ablation variants (the schemes Section 7 compares Roe-AM with; zero everywhere gives
+ * Roe-AM as defined above). A batch whose grids use any of them runs a slower kernel that
+ * evaluates every face on its scalar path.
+ *   scheme   ROEAM_SCHEME_ROEAM, or ROEAM_SCHEME_ROE: the classical Roe flux (Eq. 7 with the
+ *            eigenvalue forms of Eqs. 8-12, Delta(rho E) in the xi term). The flux then ignores
+ *            m_ref, eps1, eps2, use_s1 and xi_form, the time-step rule becomes the classical
+ *            |U| + c (theta = 1), and dup_mode, no_ufix and xi_roe must be 0.
+ *   harten   classical Roe only: eps_lambda of the entropy fix of Eqs. 114-115, in [0, 1)
+ *            (0 = no fix).
+ *   dup_mode Roe-AM delta U_p: ROEAM_DUP_ROEAM (Eq. 89), ROEAM_DUP_ZERO, or ROEAM_DUP_ROE
+ *            (max(0, c - |U|) dp / (rho c^2), the classical term of Eq. 17).
+ *   no_ufix  1: |U|' = |U| (Roe-AM without the expansion-shock fix of Eq. 92).
+ *   xi_roe   1: xi = |U| (Eq. 13) instead of Eq. 86.
+ * Out-of-range values give ROEAM_E_ARG. */
+enum { ROEAM_SCHEME_ROEAM = 0, ROEAM_SCHEME_ROE = 1 };
+enum { ROEAM_DUP_ROEAM = 0, ROEAM_DUP_ZERO = 1, ROEAM_DUP_ROE = 2 };
 typedef struct {
     double gamma, m_ref, u_ref, eps2;
     int eps1, use_s1, recon, xi_form;
     int precision;
-    int reserved_;
+    int scheme, dup_mode, no_ufix, xi_roe;
+    int reserved_;   /* must be 0 */
+    double harten;
 } roeam_params;
 
 /* One grid of ni x nj cells.
@@ -121,8 +140,9 @@ roeam_status roeam_flux_residual(roeam_grid *g, int grid_idx, double *res_out);
 /* Advances every grid by nsteps SSP-RK3 steps (Shu & Osher; each stage one fused kernel:
  * face fluxes, residual, stage combination). Each grid's dt is dt_fixed if > 0, else
  * cfl / max_i sum_dir (|U| + max(c, c~/theta))|S_dir| / V_i evaluated on the state at the
- * start of the step (theta, c~ of Eqs. 99-101). dt_last (nullable, `count` doubles)
- * receives each grid's dt of the last step (this synchronises). */
+ * start of the step (theta, c~ of Eqs. 99-101; theta = 1 on classical-Roe grids).
+ * dt_last (nullable, `count` doubles) receives each grid's dt of the last step (this
+ * synchronises). */
 roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_last);
 
 /* FP64 norm of the residual R(U) of grid `grid_idx` over its fluid cells, per variable:

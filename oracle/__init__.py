@@ -88,17 +88,22 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def make_params(p=None, *, scheme: int = 0, dup_mode: int = 0, ufix: int = 1, xi_roe: int = 0, harten: float = 0.0,
-                **over) -> OrcParams:
-    """Oracle parameter block from a workloads.SchemeParams (or keyword overrides)."""
-    d = dict(gamma=1.4, m_ref=0.5, u_ref=1.0, eps2=0.05, eps1=0, use_s1=1, recon=0, xi_form=0)
+_PARAM_NAMES = ("gamma", "m_ref", "u_ref", "eps2", "eps1", "use_s1", "recon", "xi_form", "scheme", "dup_mode",
+                "ufix", "xi_roe", "harten")
+
+
+def make_params(p=None, **over) -> OrcParams:
+    """Oracle parameter block from a workloads.SchemeParams, with keyword overrides."""
+    d = dict(gamma=1.4, m_ref=0.5, u_ref=1.0, eps2=0.05, eps1=0, use_s1=1, recon=0, xi_form=0, scheme=0,
+             dup_mode=0, ufix=1, xi_roe=0, harten=0.0)
     if p is not None:
-        d.update(gamma=p.gamma, m_ref=p.m_ref, u_ref=p.u_ref, eps2=p.eps2, eps1=p.eps1, use_s1=p.use_s1,
-                 recon=p.recon, xi_form=p.xi_form)
+        d.update({k: getattr(p, k) for k in _PARAM_NAMES if hasattr(p, k)})
+    unknown = set(over) - set(d)
+    if unknown:
+        raise TypeError(f"unknown scheme parameters {sorted(unknown)}")
     d.update(over)
-    return OrcParams(d["gamma"], d["m_ref"], d["u_ref"], d["eps2"], int(d["eps1"]), int(d["use_s1"]),
-                     int(d["recon"]), int(d["xi_form"]), int(scheme), int(dup_mode), int(ufix), int(xi_roe),
-                     float(harten))
+    return OrcParams(*(float(d[k]) if k in ("gamma", "m_ref", "u_ref", "eps2", "harten") else int(d[k])
+                       for k in _PARAM_NAMES))
 
 
 class OracleGrid:

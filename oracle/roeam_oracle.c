@@ -37,7 +37,8 @@
  *   dt      — dt = CFL / max_i sum_dir (|U| + max(c, c~/theta))_dir |S_dir| / V_i, with
  *             S_dir the means of opposite face vectors and theta, c~ of Eqs. 99-101 on
  *             the cell state, taken from U^n (the preconditioned delta U_p of Eq. 89
- *             makes the dissipation's fastest speed ~ c / M_ref at low Mach).
+ *             makes the dissipation's fastest speed ~ c / M_ref at low Mach); the
+ *             classical Roe scheme takes theta = 1, i.e. |U| + c.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -555,6 +556,8 @@ double ORC_API(orc_max_rate)(const orc_grid *g, const double *U)
     const int ni = g->ni, nj = g->nj;
     const size_t N = (size_t)ni * nj;
     real gm = (real)g->prm.gamma;
+    /* the classical Roe scheme has no preconditioned term: theta = 1 gives |U| + c */
+    real mref = g->prm.scheme == 1 ? 1 : (real)g->prm.m_ref;
     real best = 0;
     for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) {
@@ -572,8 +575,8 @@ double ORC_API(orc_max_rate)(const orc_grid *g, const double *U)
             real Yx = (real)0.5 * (ax + bx), Yy = (real)0.5 * (ay + by);
             real lx = RSQRT_(Xx * Xx + Xy * Xy), ly = RSQRT_(Yx * Yx + Yy * Yy);
             real q2 = u * u + v * v;
-            real lam = signal_speed((u * Xx + v * Xy) / lx, cs, q2, (real)g->prm.m_ref) * lx +
-                       signal_speed((u * Yx + v * Yy) / ly, cs, q2, (real)g->prm.m_ref) * ly;
+            real lam = signal_speed((u * Xx + v * Xy) / lx, cs, q2, mref) * lx +
+                       signal_speed((u * Yx + v * Yy) / ly, cs, q2, mref) * ly;
             lam /= cell_V(g, i, j);
             best = rmax(best, lam);
         }

@@ -1,7 +1,7 @@
 """Compiles the CUDA library libroeam.so in-tree for sm_103a (GB300).
 
-The three translation units (host ABI, FP32 kernels, FP64 kernels) compile in
-parallel with nvcc and link into paper_1711_09272_gb300/_build/libroeam.so.
+The five translation units (host ABI, FP32 and FP64 kernels, FP32 and FP64 ablation-variant
+kernels) compile in parallel with nvcc and link into paper_1711_09272_gb300/_build/libroeam.so.
 """
 from __future__ import annotations
 
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libroeam.so")
-SOURCES = ["roeam_api.cu", "roeam_k32.cu", "roeam_k64.cu"]
+SOURCES = ["roeam_api.cu", "roeam_k32.cu", "roeam_k64.cu", "roeam_k32_abl.cu", "roeam_k64_abl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--prec-div=false", "--prec-sqrt=false",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

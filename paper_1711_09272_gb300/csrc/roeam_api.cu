@@ -59,7 +59,7 @@ struct roeam_grid {
     int device = 0;
     cudaStream_t stream = nullptr;       // user stream (work is ordered on it)
     cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
-    int precision = 32, muscl = 0, curv = 0, walls = 0, count = 0;
+    int precision = 32, muscl = 0, curv = 0, kind = KIND_PLAIN, count = 0;   // kind: StageKind
     size_t esize = 4;
     int tile_cfg = 0;
     int nblocks = 0;        // persistent CTAs of the stage kernel
@@ -136,8 +136,8 @@ roeam_status setup_tiles(roeam_grid *g, int cfg)
     CUDA_TRY(cudaMemcpyAsync(g->d_units_grid, ug.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaMemcpyAsync(g->d_units_all, ua.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    const int occ = g->precision == 32 ? Launchers<float>::stage_occupancy(g->muscl, g->curv, g->walls)
-                                       : Launchers<double>::stage_occupancy(g->muscl, g->curv, g->walls);
+    const int occ = g->precision == 32 ? Launchers<float>::stage_occupancy(g->muscl, g->curv, g->kind)
+                                       : Launchers<double>::stage_occupancy(g->muscl, g->curv, g->kind);
     g->nblocks = std::max(1, occ * g->num_sms);
     for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
     g->graphs.clear();
@@ -175,7 +175,8 @@ roeam_status upload_coef(roeam_grid *g)
         c.gm1 = T(G.gamma - 1.0);
         c.gm1i = T(1.0 / (G.gamma - 1.0));
         c.hgm1 = T(0.5 * (G.gamma - 1.0));
-        c.mr2 = T(G.m_ref * G.m_ref);
+        // (the classical Roe flux does not use M_ref; its time-step rule is |U| + c: theta = 1)
+        c.mr2 = T(G.scheme == ROEAM_SCHEME_ROE ? 1.0 : G.m_ref * G.m_ref);
         c.rr_thr = T(1e-5 * G.u_ref);
         c.eps2 = T(G.eps2);
         c.dx = T(G.dx);
@@ -183,6 +184,7 @@ roeam_status upload_coef(roeam_grid *g)
         c.V = T(G.dx * G.dy);
         c.Vi = T(1.0 / (G.dx * G.dy));
         for (int s = 0; s < 4; ++s) c.inflow[s] = T(G.inflow[s]);
+        c.harten = T(G.harten);
     }
     CUDA_TRY(cudaMalloc(&g->d_coef, sizeof(GridCoef<T>) * g->count));
     CUDA_TRY(cudaMemcpy(g->d_coef, h.data(), sizeof(GridCoef<T>) * g->count, cudaMemcpyHostToDevice));
@@ -224,13 +226,13 @@ roeam_status launch_step(roeam_grid *g, cudaStream_t s, long long step, double c
     a.dt_fixed_t = T(dt_fixed);
     // Stage 1: U1 = U^n + dt R(U^n)
     a.src = U; a.un = U; a.dst = A; a.alpha = T(0); a.beta = T(1); a.rate_zero = wr; a.want_rate = 0;
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, s));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
     // Stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt R(U1))
     a.src = A; a.un = U; a.dst = B; a.alpha = T(0.75); a.beta = T(0.25); a.rate_zero = nullptr;
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, s));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
     // Stage 3: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt R(U2)), in place; rate of U^{n+1} for the next dt
     a.src = B; a.un = U; a.dst = U; a.alpha = T(1.0 / 3.0); a.beta = T(2.0 / 3.0); a.rate_wr = wr; a.want_rate = 1;
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, s));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
     return ROEAM_OK;
 }
 
@@ -360,7 +362,7 @@ roeam_status do_residual(roeam_grid *g, int idx, double *out)
     a.un = (const T *)g->U;
     a.dst = (T *)g->A;
     if (idx >= 0) { a.units = g->d_units_grid; a.tile_lo = g->h_tile_base[idx]; a.tile_hi = g->h_tile_base[idx + 1]; }
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, g->stream));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, g->stream));
     g->launches += 1;
     if (out) return do_get<T>(g, idx, g->A, out);
     return ROEAM_OK;
@@ -379,7 +381,7 @@ roeam_status do_norm(roeam_grid *g, int idx, int kind, double out[4])
     a.partials = g->partials;
     const int nb = std::min(g->nblocks, std::min(g->partial_rows, a.tile_hi - a.tile_lo));
     CUDA_TRY(cudaMemsetAsync(g->partials, 0, sizeof(double) * 8 * g->partial_rows, g->stream));
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, nb, g->stream));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, nb, g->stream));
     CUDA_TRY(launch_reduce_partials(g->partials, nb, 8, g->red_out, g->stream));
     g->launches += 2;
     CUDA_TRY(cudaMemcpyAsync(g->h_red, g->red_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, g->stream));
@@ -421,6 +423,18 @@ roeam_status validate(int count, const roeam_grid_desc *d)
         if (p.use_s1 != 0 && p.use_s1 != 1) return fail(ROEAM_E_ARG, "grid %d: use_s1 must be 0 or 1", k);
         if (p.xi_form != 0 && p.xi_form != 1) return fail(ROEAM_E_ARG, "grid %d: xi_form must be 0 or 1", k);
         if (p.recon < 0 || p.recon > 2) return fail(ROEAM_E_ARG, "grid %d: recon must be 0, 1 or 2", k);
+        if (p.scheme != ROEAM_SCHEME_ROEAM && p.scheme != ROEAM_SCHEME_ROE)
+            return fail(ROEAM_E_ARG, "grid %d: scheme must be ROEAM_SCHEME_ROEAM or ROEAM_SCHEME_ROE", k);
+        if (p.dup_mode < ROEAM_DUP_ROEAM || p.dup_mode > ROEAM_DUP_ROE)
+            return fail(ROEAM_E_ARG, "grid %d: dup_mode must be 0, 1 or 2", k);
+        if (p.no_ufix != 0 && p.no_ufix != 1) return fail(ROEAM_E_ARG, "grid %d: no_ufix must be 0 or 1", k);
+        if (p.xi_roe != 0 && p.xi_roe != 1) return fail(ROEAM_E_ARG, "grid %d: xi_roe must be 0 or 1", k);
+        if (p.reserved_ != 0) return fail(ROEAM_E_ARG, "grid %d: reserved_ must be 0", k);
+        if (!(p.harten >= 0.0 && p.harten < 1.0)) return fail(ROEAM_E_ARG, "grid %d: harten must be in [0, 1)", k);
+        if (p.scheme == ROEAM_SCHEME_ROE && (p.dup_mode || p.no_ufix || p.xi_roe))
+            return fail(ROEAM_E_ARG, "grid %d: dup_mode, no_ufix and xi_roe are Roe-AM variants (scheme is ROE)", k);
+        if (p.scheme == ROEAM_SCHEME_ROEAM && p.harten != 0.0)
+            return fail(ROEAM_E_ARG, "grid %d: harten applies to the classical Roe scheme only", k);
         if (p.precision != 32 && p.precision != 64) return fail(ROEAM_E_ARG, "grid %d: precision must be 32 or 64", k);
         if (p.precision != d[0].p.precision) return fail(ROEAM_E_ARG, "grid %d: precision differs within the batch", k);
         if ((p.recon > 0) != (d[0].p.recon > 0))
@@ -507,14 +521,23 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
         poff += 4ll * q.ni * q.nj;
         g->max_cells = std::max(g->max_cells, q.ni * q.nj);
         for (int s = 0; s < 4; ++s) G.bc[s] = q.bc[s];
+        bool walls = q.solid != nullptr;
         for (int s = 0; s < 4; ++s)
-            if (q.bc[s] == ROEAM_BC_WALL) g->walls = 1;
-        if (q.solid) g->walls = 1;
+            if (q.bc[s] == ROEAM_BC_WALL) walls = true;
+        const bool ablation = q.p.scheme != ROEAM_SCHEME_ROEAM || q.p.dup_mode != ROEAM_DUP_ROEAM || q.p.no_ufix ||
+                              q.p.xi_roe;
+        if (ablation) g->kind = KIND_ABLATION;
+        else if (walls && g->kind == KIND_PLAIN) g->kind = KIND_WALLS;
         for (int s = 0; s < 4; ++s) G.inflow[s] = q.inflow[s];
         G.limiter = q.p.recon;
         G.eps1 = q.p.eps1;
         G.use_s1 = q.p.use_s1;
         G.xi_form = q.p.xi_form;
+        G.scheme = q.p.scheme;
+        G.dup_mode = q.p.dup_mode;
+        G.ufix = q.p.no_ufix ? 0 : 1;
+        G.xi_roe = q.p.xi_roe;
+        G.harten = q.p.harten;
         G.gamma = q.p.gamma;
         G.m_ref = q.p.m_ref;
         G.u_ref = q.p.u_ref;
@@ -860,7 +883,7 @@ roeam_status do_residual_noalloc(roeam_grid *g, int idx, double *out)
     a.units = g->d_units_grid;
     a.tile_lo = g->h_tile_base[idx];
     a.tile_hi = g->h_tile_base[idx + 1];
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->walls, g->nblocks, g->stream));
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, g->stream));
     CUDA_TRY(Launchers<T>::unpack(g->d_grids, idx, idx + 1, G.ni * G.nj, (const T *)base_t, (double *)base_d,
                                   g->stream));
     g->launches += 2;

@@ -1,6 +1,6 @@
 // roeam_internal.h — device-side descriptors and launch entry points shared by the
 // library's host code (roeam_api.cu) and its kernel translation units (roeam_k32.cu,
-// roeam_k64.cu). Not part of the public ABI.
+// roeam_k64.cu and their ablation-variant companions). Not part of the public ABI.
 #pragma once
 
 #include <cstdint>
@@ -25,8 +25,10 @@ struct GridDev {
     int bc[4];        // W, E, S, N
     int limiter;      // 1 minmod, 2 van Leer (MUSCL kernels)
     int eps1, use_s1, xi_form;
+    int scheme, dup_mode, ufix, xi_roe;   // ablation variants (0, 0, 1, 0: Roe-AM)
     double inflow[4]; // rho, u, v, p
     double gamma, m_ref, u_ref, eps2;
+    double harten;    // classical Roe: eps_lambda of the entropy fix (0: none)
     double dx, dy;    // Cartesian spacings / reference-grid spacings of a curvilinear grid
     double nfluid;    // number of fluid cells
 };
@@ -40,6 +42,7 @@ struct GridCoef {
     T g, gm1, gm1i, hgm1, mr2, rr_thr, eps2;   // gamma, gamma-1, 1/(gamma-1), (gamma-1)/2, M_ref^2, 1e-5 U_ref, eps2
     T dx, dy, V, Vi;                     // spacings (reference spacings if curvilinear), dx*dy, 1/(dx*dy)
     T inflow[4];                         // rho, u, v, p of INFLOW sides
+    T harten;                            // classical Roe: eps_lambda (0: no entropy fix)
 };
 
 template <typename T>
@@ -77,30 +80,33 @@ constexpr int STAGE_THREADS = STAGE_THREADS_DEF;
 // Resident CTAs per SM the compiler is asked to fit (register budget): 13 keeps the FP32
 // first-order Cartesian kernel at 128 registers without spills (16 warps per SM); the
 // reconstructing and curvilinear FP32 variants stay at ~168 registers (12 warps) where they
-// do not spill; FP64 is left to the compiler.
+// do not spill; FP64 and the ablation variants are left to the compiler.
 #ifndef STAGE_MIN_BLOCKS_FAST
 #define STAGE_MIN_BLOCKS_FAST 13
 #endif
 #ifndef STAGE_MIN_BLOCKS_OTHER
 #define STAGE_MIN_BLOCKS_OTHER 12
 #endif
-template <typename T, bool MUSCL, bool CURV>
+template <typename T, bool MUSCL, bool CURV, bool ABL = false>
 constexpr int stage_min_blocks()
 {
-    return sizeof(T) != 4 ? 1 : ((!MUSCL && !CURV) ? STAGE_MIN_BLOCKS_FAST : STAGE_MIN_BLOCKS_OTHER);
+    return (sizeof(T) != 4 || ABL) ? 1 : ((!MUSCL && !CURV) ? STAGE_MIN_BLOCKS_FAST : STAGE_MIN_BLOCKS_OTHER);
 }
 struct TileCfg { int tx, ty, nt; };
 constexpr int NUM_TILE_CFGS = 4;
 constexpr TileCfg TILE_CFGS[NUM_TILE_CFGS] = {{32, 32, STAGE_THREADS}, {32, 64, STAGE_THREADS},
                                               {32, 16, STAGE_THREADS}, {32, 128, STAGE_THREADS}};
 
+// Stage-kernel families: no walls anywhere in the batch; some WALL side or solid cells; some
+// grid uses an ablation variant of the flux (every face on the scalar path).
+enum StageKind { KIND_PLAIN = 0, KIND_WALLS = 1, KIND_ABLATION = 2 };
+
 template <typename T>
 struct Launchers {
     // Fused face-flux / residual / stage kernel over tiles [tile_lo, tile_hi).
-    // walls: some grid of the batch has a WALL side or solid cells.
-    static cudaError_t stage(const StageArgs<T> &a, int muscl, int curv, int walls, int nblocks, cudaStream_t s);
+    static cudaError_t stage(const StageArgs<T> &a, int muscl, int curv, int kind, int nblocks, cudaStream_t s);
     // Largest resident CTAs per SM of a stage-kernel variant (for persistent launches).
-    static int stage_occupancy(int muscl, int curv, int walls);
+    static int stage_occupancy(int muscl, int curv, int kind);
     // Max signal-speed rate of a state into rate[g] (slot zeroed first by the caller).
     static cudaError_t rate(const GridDev *grids, const GridCoef<T> *coef, int g_lo, int g_hi, const T *U,
                             const T *vdx, const T *vdy, const uint8_t *solid, unsigned long long *rate, int curv,
@@ -114,6 +120,13 @@ struct Launchers {
     static cudaError_t totals(const GridDev *grids, const GridCoef<T> *coef, int g, const T *U, const T *vdx,
                               const T *vdy, const uint8_t *solid, double *partials, int nblocks, int curv,
                               cudaStream_t s);
+};
+
+// The ablation-variant stage kernels, instantiated in their own translation units.
+template <typename T>
+struct AblationLaunchers {
+    static cudaError_t stage(const StageArgs<T> &a, int muscl, int curv, int nblocks, cudaStream_t s);
+    static int stage_occupancy(int muscl, int curv);
 };
 
 // Fixed-order reduction of nblocks x 8 norm partials into out[8] (sum[4], max[4]).

@@ -3,5 +3,6 @@
 #include "roeam_kernels.cuh"
 
 namespace roeam {
+extern template struct AblationLaunchers<float>;   // in roeam_k32_abl.cu
 template struct Launchers<float>;
 }

@@ -2,6 +2,7 @@
 #include "roeam_kernels.cuh"
 
 namespace roeam {
+extern template struct AblationLaunchers<double>;   // in roeam_k64_abl.cu
 template struct Launchers<double>;
 
 // Fixed-order reduction of nblocks rows of `width` partials (first half sums, second half

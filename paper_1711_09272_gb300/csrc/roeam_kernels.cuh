@@ -158,16 +158,22 @@ __device__ __forceinline__ FS<V> side_from_prims(V r, V un, V ut, V p, const Gri
     return s;
 }
 
+// Ablation variants of the flux (the schemes Section 7 compares with), read per grid by the
+// ablation kernels only: scheme 1 is classical Roe (Eq. 7 with Eqs. 8-12, entropy fix of
+// Eqs. 114-115 with GridCoef::harten); for Roe-AM, dup_mode 1 sets delta U_p = 0 and 2 takes
+// the Roe term of Eq. 17, ufix = 0 drops Eq. 92, xi_roe = 1 takes xi = |U| (Eq. 13).
+struct Variant { int scheme = 0, dup_mode = 0, ufix = 1, xi_roe = 0; };
+
 // Twice the Roe-AM numerical flux per unit face length, in the face frame (components:
 // mass, normal momentum, tangential momentum, energy). Section 6.2, term by term:
 // central part (Eqs. 3-4), Roe averages, M (Eq. 93), Mbar (Eq. 94), f (Eq. 98), |U|'
 // (Eq. 92, clamped at 0), xi (Eq. 86 with the Eq. 68 factor unless xi_form = 1; the eps1
 // floor with Eqs. 102-109), delta p_p + delta p_u (Eqs. 87-88), rho delta U_p (Eq. 89 with
 // Eqs. 99-101), delta U_u (Eqs. 90-91), assembled as Eq. 85 with the energy convention of
-// Eq. 49.
-template <typename V, typename S>
+// Eq. 49. With ABL the Variant switches apply (scalar V only).
+template <bool ABL = false, typename V, typename S>
 __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1, const GridCoef<S> &K, int eps1,
-                                            int xi_form, V F[4])
+                                            int xi_form, V F[4], const Variant &var = Variant())
 {
     const V zero = splat<V>(0), one = splat<V>(1), half = splat<V>(S(0.5));
     const V mL = L.r * L.un, mR = R.r * R.un;
@@ -189,6 +195,34 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     const V ch = c2h * chi;
     const V aU = vabs(uh);
 
+    if constexpr (ABL) {
+        if (var.scheme == 1) {
+            // Classical Roe: |lambda| = |U|, |U - c|, |U + c|, each raised to (l^2 / h + h) / 2
+            // below h = eps_lambda max|lambda| (Eqs. 114-115); xi = l1 (Eq. 8), delta p_u +
+            // delta p_p (Eqs. 9-10) and rho (delta U_u + delta U_p) (Eqs. 11-12); the xi term
+            // acts on Delta(rho E) = Delta(rho H) - Delta p and the pressure vector carries U
+            // in its energy slot.
+            V l1 = aU, l4 = vabs(uh - ch), l5 = vabs(uh + ch);
+            const V hh = splat<V>(K.harten) * vmax(l1, vmax(l4, l5));
+            if (gt(hh, zero)) {
+                const V hi = rcp(hh);
+                l1 = sel(lt(l1, hh), half * vfma(l1 * l1, hi, hh), l1);
+                l4 = sel(lt(l4, hh), half * vfma(l4 * l4, hi, hh), l4);
+                l5 = sel(lt(l5, hh), half * vfma(l5 * l5, hi, hh), l5);
+            }
+            const V dp = R.p - L.p;
+            const V spp = vfma(half, l5 + l4, -l1), smm = half * (l5 - l4);
+            const V pp = vfma(spp * rh, du, smm * dp * chi);
+            const V A = vfma(smm * rh * chi, du, spp * dp * chi * chi);
+            const V QL2 = L.r * L.ut, QR2 = R.r * R.ut, QL3 = L.r * L.H, QR3 = R.r * R.H;
+            F[0] = F0c - vfma(l1, R.r - L.r, A);
+            F[1] = F1c - vfma(l1, mR - mL, vfma(A, uh, pp));
+            F[2] = F2c - vfma(l1, QR2 - QL2, A * vh);
+            F[3] = F3c - vfma(l1, (QR3 - QL3) - dp, vfma(A, Hh, pp * uh));
+            return;
+        }
+    }
+
     const V M = half * (L.Mq + R.Mq);
     const V Mb = aU * chi;
     const V fM = fmach(M), fMb = fmach(Mb);
@@ -197,7 +231,10 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
 
     // |U|': the bracket sgn(U + c) - sgn(U - c) is 2 for |U| < c, 1 for |U| = c, 0 above.
     const V br = sel(lt(aU, ch), splat<V>(2), sel(eq(aU, ch), one, zero));
-    const V Up = sel(gt(du, zero), vmax(vfma(splat<V>(S(-0.25)) * fMb * br, du, aU), zero), aU);
+    V Up = sel(gt(du, zero), vmax(vfma(splat<V>(S(-0.25)) * fMb * br, du, aU), zero), aU);
+    if constexpr (ABL) {
+        if (!var.ufix) Up = aU;
+    }
 
     const V xfac = xi_form ? one : one - fMb8;
     V xi = vmax(vfma(xfac * half, du, vabs(half * (L.un + R.un))), zero);
@@ -210,6 +247,9 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
         const V n1x = sel(big, du * dqi, one), n1y = sel(big, dv * dqi, zero);
         const V frr = vabs(n1x * vfma(n1x, uh, n1y * vh)) + vabs(n1y * (vfma(n1x, vh, -(n1y * uh))));
         xi = vmax(xi, (one - fMb8) * fM8 * vmin(splat<V>(K.eps2) * ch, frr));
+    }
+    if constexpr (ABL) {
+        if (var.xi_roe) xi = aU;
     }
 
     // sgn(U) min(|U|', c): min(|U|', c) = 0 whenever U = 0 (then |U|' = 0), so the sign can
@@ -225,7 +265,11 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     const V Ut = half * (one + th) * uh;
     // U sgn(U~) min(|U~|, c~) = |U| min(|U~|, c~): U~ = (1 + theta) U / 2 has the sign of U
     const V term = vfma(om, Up - aU * rX * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
-    const V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
+    V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
+    if constexpr (ABL) {
+        if (var.dup_mode == 1) A = zero;
+        else if (var.dup_mode == 2) A = vmax(ch - aU, zero) * dp * chi * chi;   // rho x Eq. 17
+    }
     const V dUu = half * smc * du;
 
     const V QL2 = L.r * L.ut, QR2 = R.r * R.ut, QL3 = L.r * L.H, QR3 = R.r * R.H;
@@ -403,9 +447,9 @@ __device__ __forceinline__ void muscl_states(bool vanleer, const V Am[4], const 
 // Scalar evaluation of one face: walls (first-order state and its mirror), MUSCL with solid
 // mirrors and the FP64 positivity decision in FP32, rotation to the face frame, flux, and the
 // rotation back. Returns F |S| in the global frame.
-template <typename T, bool MUSCL>
+template <typename T, bool MUSCL, bool ABL = false>
 __device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> &K, int eps1, int xi_form,
-                                            bool vanleer, T F[4])
+                                            bool vanleer, T F[4], const Variant &var = Variant())
 {
     F[0] = F[1] = F[2] = F[3] = T(0);
     if ((f.A.fl & f.B.fl) & 1) return;
@@ -444,7 +488,7 @@ __device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> 
         R = side_rot(WR[0], WR[1], WR[2], WR[3], f.nx, f.ny, K);
     }
     T G2[4];
-    roeam_flux2(L, R, f.s1, K, eps1, xi_form, G2);
+    roeam_flux2<ABL>(L, R, f.s1, K, eps1, xi_form, G2, var);
     const T h = T(0.5) * f.len;
     F[0] = h * G2[0];
     F[1] = h * (f.nx * G2[1] - f.ny * G2[2]);
@@ -607,8 +651,8 @@ template <bool WALLS, typename T> __device__ __forceinline__ WC<T> shdn_c(const 
     return o;
 }
 
-template <typename T, bool MUSCL, bool CURV, bool WALLS, int NT>
-__global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV>())) stage_kernel(const StageArgs<T> a)
+template <typename T, bool MUSCL, bool CURV, bool WALLS, int NT, bool ABL>
+__global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>())) stage_kernel(const StageArgs<T> a)
 {
     constexpr int H = MUSCL ? 2 : 1;
     constexpr int NW = H + 2;          // window rows j-H .. j+1
@@ -644,6 +688,10 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV>())) stag
         const bool use_s1 = G.use_s1 != 0;
         const int eps1 = G.eps1, xi_form = G.xi_form;
         const bool vanleer = G.limiter == 2;
+        Variant var;
+        if constexpr (ABL) {
+            var.scheme = G.scheme; var.dup_mode = G.dup_mode; var.ufix = G.ufix; var.xi_roe = G.xi_roe;
+        }
         int kx;
         const int isrc = resolve_index(i, ni, R.bcW, R.bcE, kx);
         const bool icol = i >= 0 && i < ni;
@@ -764,10 +812,10 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV>())) stag
             }
 
             T Fw[4], Fs[4];
-            // walls, solid cells (and FP64) take the scalar path; batches without walls or solid
-            // cells never do in FP32
-            bool scalar = !PACKED;
-            if constexpr (PACKED && WALLS)
+            // walls, solid cells (and FP64, and the ablation variants) take the scalar path;
+            // batches without walls or solid cells never do in FP32
+            bool scalar = !PACKED || ABL;
+            if constexpr (PACKED && WALLS && !ABL)
                 scalar = __any_sync(0xffffffffu, face_is_wall(fx, MUSCL) || face_is_wall(fy, MUSCL));
             if constexpr (PACKED && MUSCL) {
                 // an FP32 reconstruction within rounding of zero is decided in FP64 (scalar path)
@@ -785,8 +833,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV>())) stag
             }
             if (scalar) {
                 if constexpr (!PACKED || WALLS || MUSCL) {
-                    face_scalar<T, MUSCL>(fx, K, eps1, xi_form, vanleer, Fw);
-                    face_scalar<T, MUSCL>(fy, K, eps1, xi_form, vanleer, Fs);
+                    face_scalar<T, MUSCL, ABL>(fx, K, eps1, xi_form, vanleer, Fw, var);
+                    face_scalar<T, MUSCL, ABL>(fy, K, eps1, xi_form, vanleer, Fs, var);
                 }
             } else if constexpr (PACKED) {
                 faces_packed<MUSCL, CURV>(fx, fy, K, eps1, xi_form, vanleer, Fw, Fs);
@@ -992,17 +1040,17 @@ __global__ void __launch_bounds__(256) totals_kernel(const GridDev *grids, const
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, bool MUSCL, bool CURV, bool WALLS> struct StageVariant {
+template <typename T, bool MUSCL, bool CURV, bool WALLS, bool ABL = false> struct StageVariant {
     static constexpr int NT = STAGE_THREADS;
     static cudaError_t launch(const StageArgs<T> &a, int nblocks, cudaStream_t s)
     {
-        stage_kernel<T, MUSCL, CURV, WALLS, NT><<<nblocks, NT, 0, s>>>(a);
+        stage_kernel<T, MUSCL, CURV, WALLS, NT, ABL><<<nblocks, NT, 0, s>>>(a);
         return cudaGetLastError();
     }
     static int occupancy()
     {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T, MUSCL, CURV, WALLS, NT>, NT, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T, MUSCL, CURV, WALLS, NT, ABL>, NT, 0) !=
             cudaSuccess)
             return 1;
         return n > 0 ? n : 1;
@@ -1022,18 +1070,44 @@ static int occ_walls(int walls)
 }
 
 template <typename T>
-cudaError_t Launchers<T>::stage(const StageArgs<T> &a, int muscl, int curv, int walls, int nblocks, cudaStream_t s)
+cudaError_t Launchers<T>::stage(const StageArgs<T> &a, int muscl, int curv, int kind, int nblocks, cudaStream_t s)
 {
     if (a.tile_hi <= a.tile_lo) return cudaSuccess;
+    if (kind == KIND_ABLATION) return AblationLaunchers<T>::stage(a, muscl, curv, nblocks, s);
+    const int walls = kind == KIND_WALLS;
     if (muscl) return curv ? stage_walls<T, true, true>(a, walls, nblocks, s) : stage_walls<T, true, false>(a, walls, nblocks, s);
     return curv ? stage_walls<T, false, true>(a, walls, nblocks, s) : stage_walls<T, false, false>(a, walls, nblocks, s);
 }
 
 template <typename T>
-int Launchers<T>::stage_occupancy(int muscl, int curv, int walls)
+int Launchers<T>::stage_occupancy(int muscl, int curv, int kind)
 {
+    if (kind == KIND_ABLATION) return AblationLaunchers<T>::stage_occupancy(muscl, curv);
+    const int walls = kind == KIND_WALLS;
     if (muscl) return curv ? occ_walls<T, true, true>(walls) : occ_walls<T, true, false>(walls);
     return curv ? occ_walls<T, false, true>(walls) : occ_walls<T, false, false>(walls);
+}
+
+// The ablation kernels handle walls and solid cells too (every face takes the scalar path).
+template <typename T>
+cudaError_t AblationLaunchers<T>::stage(const StageArgs<T> &a, int muscl, int curv, int nblocks, cudaStream_t s)
+{
+    if (a.tile_hi <= a.tile_lo) return cudaSuccess;
+    if (muscl)
+        return curv ? StageVariant<T, true, true, true, true>::launch(a, nblocks, s)
+                    : StageVariant<T, true, false, true, true>::launch(a, nblocks, s);
+    return curv ? StageVariant<T, false, true, true, true>::launch(a, nblocks, s)
+                : StageVariant<T, false, false, true, true>::launch(a, nblocks, s);
+}
+
+template <typename T>
+int AblationLaunchers<T>::stage_occupancy(int muscl, int curv)
+{
+    if (muscl)
+        return curv ? StageVariant<T, true, true, true, true>::occupancy()
+                    : StageVariant<T, true, false, true, true>::occupancy();
+    return curv ? StageVariant<T, false, true, true, true>::occupancy()
+                : StageVariant<T, false, false, true, true>::occupancy();
 }
 
 template <typename T>

@@ -37,7 +37,8 @@ class RoeamError(RuntimeError):
 class roeam_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("m_ref", C.c_double), ("u_ref", C.c_double), ("eps2", C.c_double),
                 ("eps1", C.c_int), ("use_s1", C.c_int), ("recon", C.c_int), ("xi_form", C.c_int),
-                ("precision", C.c_int), ("reserved_", C.c_int)]
+                ("precision", C.c_int), ("scheme", C.c_int), ("dup_mode", C.c_int), ("no_ufix", C.c_int),
+                ("xi_roe", C.c_int), ("reserved_", C.c_int), ("harten", C.c_double)]
 
 
 class roeam_grid_desc(C.Structure):
@@ -210,7 +211,9 @@ def make_desc(spec, precision: int = 64, keep: Optional[list] = None) -> roeam_g
         d.solid = s.ctypes.data_as(C.POINTER(C.c_uint8))
     p = spec.params
     d.p = roeam_params(p.gamma, p.m_ref, p.u_ref, p.eps2, int(p.eps1), int(p.use_s1), int(p.recon),
-                       int(p.xi_form), int(precision), 0)
+                       int(p.xi_form), int(precision), int(getattr(p, "scheme", 0)), int(getattr(p, "dup_mode", 0)),
+                       0 if int(getattr(p, "ufix", 1)) else 1, int(getattr(p, "xi_roe", 0)), 0,
+                       float(getattr(p, "harten", 0.0)))
     return d
 
 

@@ -54,3 +54,9 @@ def test_create_rejects_bad_arguments_without_gpu_work():
     with pytest.raises(P.RoeamError) as e:
         P.roeam_create_grid([a, b])
     assert "precision" in str(e.value)
+    for kw, word in ((dict(scheme=2), "scheme"), (dict(dup_mode=3), "dup_mode"), (dict(harten=0.1), "harten"),
+                     (dict(scheme=1, dup_mode=1), "Roe-AM variants"), (dict(scheme=1, harten=1.0), "harten"),
+                     (dict(xi_roe=2), "xi_roe")):
+        with pytest.raises(P.RoeamError) as e:
+            P.roeam_create_grid([P.make_desc(W.with_params(W.GridSpec(ni=8, nj=8), **kw))])
+        assert e.value.status == 1 and word in str(e.value), (kw, str(e.value))

@@ -52,6 +52,18 @@ CASES = {
                                                  params=W.SchemeParams(m_ref=0.8, recon=2, eps1=1)), 2.5),
     "no_detector_xi_literal": lambda: (W.GridSpec(ni=40, nj=33, params=W.SchemeParams(use_s1=0, xi_form=1)), 1.5),
     "low_mach": lambda: (W.GridSpec(ni=48, nj=40, params=W.SchemeParams(m_ref=1e-3, recon=1)), 0.01),
+    # ablation variants of Section 7
+    "roe": lambda: (W.GridSpec(ni=45, nj=38, dx=0.013, dy=0.021, params=W.SchemeParams(scheme=1)), 1.2),
+    "roe_harten_minmod": lambda: (W.GridSpec(ni=44, nj=35, params=W.SchemeParams(scheme=1, harten=0.2, recon=1)),
+                                  1.5),
+    "roe_harten_low_mach": lambda: (W.GridSpec(ni=40, nj=36, params=W.SchemeParams(scheme=1, harten=0.05,
+                                                                                      m_ref=1e-2)), 0.01),
+    "roeam_dup_zero": lambda: (W.GridSpec(ni=41, nj=37, params=W.SchemeParams(dup_mode=1, m_ref=0.05)), 0.05),
+    "roeam_dup_roe_vanleer": lambda: (W.GridSpec(ni=43, nj=34, params=W.SchemeParams(dup_mode=2, recon=2,
+                                                                                     m_ref=0.05)), 0.05),
+    "roeam_no_ufix": lambda: (W.GridSpec(ni=42, nj=39, params=W.SchemeParams(ufix=0, m_ref=0.5)), 1.2),
+    "roeam_roe_xi_and_dup_eps1": lambda: (W.GridSpec(ni=47, nj=33, params=W.SchemeParams(xi_roe=1, dup_mode=2,
+                                                                                         eps1=1)), 1.5),
 }
 
 
@@ -189,3 +201,36 @@ def test_nonpositive_state_is_reported():
             b.check()
         assert e.value.status in (4, 5)
         b.check()   # the status was cleared
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("variant", [dict(scheme=1, harten=0.05), dict(xi_roe=1, dup_mode=2)])
+def test_step_parity_ablation_walls_and_curvilinear(prec, variant):
+    """The ablation kernels on the duct (walls, inflow, outflow, MUSCL) and on a warped
+    periodic grid."""
+    spec, U = W.quirk(nx=60, ny=20, eps_y=0.1, x_shock=20.0, recon=2)
+    spec = W.with_params(spec, **variant)
+    assert one_step_parity(spec, U, prec, cfl=0.4) <= TOL[prec]
+    spec = W.with_params(W.warped_periodic(36, amp=0.2), m_ref=0.4, **variant)
+    U = W.random_smooth_state(spec, seed=12, mach=0.7, amp=0.5)
+    assert one_step_parity(spec, U, prec) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_batch_mixing_schemes(prec):
+    """One batch holding Roe-AM, classical Roe (with and without the entropy fix) and Roe-AM
+    variants: each grid follows the oracle with its own scheme."""
+    base = dict(ni=37, nj=29, dx=0.02, dy=0.03)
+    plist = [W.SchemeParams(), W.SchemeParams(scheme=1), W.SchemeParams(scheme=1, harten=0.1),
+             W.SchemeParams(dup_mode=1), W.SchemeParams(ufix=0, xi_roe=1)]
+    specs = [W.GridSpec(params=p, **base) for p in plist]
+    states = [W.random_rough_state(s, seed=300 + k, mach=0.9, jump=0.3) for k, s in enumerate(specs)]
+    with P().Batch(specs, precision=prec) as b:
+        b.set_states(states)
+        U0 = b.get_states()
+        dts = b.step(0.5, nsteps=1, want_dt=True)
+        U1 = b.get_states()
+    for k, s in enumerate(specs):
+        Uo, dto = oracle.OracleGrid(s).step(U0[k], cfl=0.5)
+        assert abs(dts[k] - dto) <= 1e-5 * dto
+        assert rel_state_err(U1[k], Uo) <= TOL[prec], k

@@ -214,16 +214,25 @@ def test_expansion_shock_removed_by_eq92():
     full, _ = run_tube("expansion", 200)
     nofix, _ = run_tube("expansion", 200, ufix=0)
     roe, _ = run_tube("expansion", 200, scheme=1)
+    harten, _ = run_tube("expansion", 200, scheme=1, harten=0.2)
     assert max_jump(full) < 0.15
     assert max_jump(nofix) > 0.5 and max_jump(roe) > 0.5
+    assert max_jump(harten) < 0.15   # the entropy fix of Eqs. 114-115 also removes it
 
 
 def test_near_vacuum_positivity():
-    """Section 7.1.2: Roe-AM keeps rho, p > 0 in the near-vacuum test; classical Roe fails."""
+    """Section 7.1.2: Roe-AM keeps rho, p > 0 in the near-vacuum test; classical Roe fails
+    (Section 4.3: the positivity conditions)."""
     U, _ = run_tube("near_vacuum", 200)
     assert U is not None
     U_roe, _ = run_tube("near_vacuum", 200, scheme=1)
     assert U_roe is None
+    # the velocity-positivity form of xi (Eq. 86) is what keeps Roe-AM positive here: with
+    # xi = |U| of Eq. 13 it fails like Roe; the Roe form of delta U_p does not matter
+    U_xi, _ = run_tube("near_vacuum", 200, xi_roe=1)
+    assert U_xi is None
+    U_dup, _ = run_tube("near_vacuum", 200, dup_mode=2)
+    assert U_dup is not None
 
 
 # ----------------------------------------------------------------------------- low Mach
@@ -276,3 +285,16 @@ def test_isentropic_vortex_convergence(recon, order):
         errs.append(float(np.sqrt(np.mean((U[0] - Ue[0]) ** 2))))
     rates = [math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])]
     assert min(rates) > order, (errs, rates)
+
+
+def test_classical_roe_time_step_rule():
+    """The classical Roe scheme takes theta = 1 in the time-step rule: on a Cartesian grid the
+    rate is max_i (|u| + c) / dx + (|v| + c) / dy (closed form); Roe-AM at low M_ref is faster."""
+    spec = W.GridSpec(ni=12, nj=9, dx=0.1, dy=0.07, params=W.SchemeParams(m_ref=0.05, scheme=1))
+    U = W.random_smooth_state(spec, seed=4, mach=0.3, amp=0.3)
+    rho, u, v, p = W.cons_to_prim(U)
+    c = np.sqrt(1.4 * p / rho)
+    ref = np.max((np.abs(u) + c) / spec.dx + (np.abs(v) + c) / spec.dy)
+    rate = oracle.OracleGrid(spec).max_rate(U)
+    assert abs(rate - ref) <= 1e-14 * ref
+    assert oracle.OracleGrid(W.with_params(spec, scheme=0)).max_rate(U) > 2 * ref

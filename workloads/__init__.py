@@ -38,6 +38,12 @@ class SchemeParams:
     the pressure-density detector of Eq. 95, 0 sets s1 = 1 (Eq. 110).
     recon: 0 first order, 1 MUSCL minmod, 2 MUSCL van Leer (primitive variables).
     xi_form: 0 keeps the [1 - f^8(Mbar)] factor of Eq. 68 on dU/2 in xi, 1 is Eq. 86 literally.
+
+    Ablation variants of Section 7 (all defaults give Roe-AM as defined in Section 6.2):
+    scheme: 0 Roe-AM, 1 classical Roe (Eq. 7 with Eqs. 8-12); harten: its entropy-fix
+    constant eps_lambda of Eqs. 114-115 (0 = none); dup_mode: delta U_p of Roe-AM by Eq. 89 (0),
+    zero (1), or the Roe form of Eq. 17 (2); ufix: 1 applies Eq. 92, 0 keeps |U|; xi_roe: 1
+    takes xi = |U| (Eq. 13) in Roe-AM.
     """
     gamma: float = GAMMA
     m_ref: float = 0.5
@@ -47,6 +53,11 @@ class SchemeParams:
     use_s1: int = 1
     recon: int = RECON_FIRST
     xi_form: int = 0
+    scheme: int = 0
+    dup_mode: int = 0
+    ufix: int = 1
+    xi_roe: int = 0
+    harten: float = 0.0
 
 
 @dataclass
