@@ -98,10 +98,16 @@ typedef struct {
  *              OUTFLOW copies the adjacent state (zero gradient).
  *   inflow     (rho, u, v, p) used by INFLOW sides.
  *   xv, yv     host float64 vertex coordinates, shape [nj+1][ni+1], or both NULL for a
- *              Cartesian grid with spacings dx, dy. For curvilinear grids dx, dy give
- *              the uniform reference grid x = i*dx, y = j*dy that the library stores
+ *              Cartesian grid with spacings dx, dy (> 0). For curvilinear grids dx, dy >= 0
+ *              give the uniform reference grid x = i*dx, y = j*dy that the library stores
  *              the vertices relative to (the displacement from it is kept in the working
- *              precision), so they should be the mean spacings.
+ *              precision): the mean spacings for a gently warped grid; 0, 0 (absolute
+ *              coordinates) for grids such as O-grids, whose cells shrink towards the
+ *              origin. Every cell must have positive area (the vertex order turns
+ *              counter-clockwise from +i to +j), else ROEAM_E_ARG. A periodic direction
+ *              should repeat its first vertex column (row) in the last one up to the
+ *              period shift, bit for bit after the subtraction of the reference grid, so
+ *              that both sides of the seam see the same face.
  *   solid      host uint8 mask [nj][ni] (1 = solid wall cell, never updated) or NULL.
  *              Solid cells may not be combined with PERIODIC in the same direction. */
 typedef struct {

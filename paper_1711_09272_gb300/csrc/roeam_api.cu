@@ -442,7 +442,23 @@ roeam_status validate(int count, const roeam_grid_desc *d)
         if ((q.xv != nullptr) != (q.yv != nullptr)) return fail(ROEAM_E_ARG, "grid %d: give both xv and yv or neither", k);
         if ((q.xv != nullptr) != (d[0].xv != nullptr))
             return fail(ROEAM_E_ARG, "grid %d: Cartesian and curvilinear grids cannot share a batch", k);
-        if (!(q.dx > 0.0) || !(q.dy > 0.0)) return fail(ROEAM_E_ARG, "grid %d: dx, dy must be > 0", k);
+        if (!q.xv && (!(q.dx > 0.0) || !(q.dy > 0.0))) return fail(ROEAM_E_ARG, "grid %d: dx, dy must be > 0", k);
+        if (q.xv && (!(q.dx >= 0.0) || !(q.dy >= 0.0) || !std::isfinite(q.dx) || !std::isfinite(q.dy)))
+            return fail(ROEAM_E_ARG, "grid %d: reference spacings dx, dy must be >= 0", k);
+        if (q.xv) {
+            // every cell must have positive area: vertices ordered so that i x j points out of the plane
+            const int W = q.ni + 1;
+            for (int J = 0; J < q.nj; ++J)
+                for (int I = 0; I < q.ni; ++I) {
+                    const size_t a = (size_t)J * W + I, b = a + W + 1, c = a + W, e = a + 1;
+                    const double A = 0.5 * ((q.xv[b] - q.xv[a]) * (q.yv[c] - q.yv[e]) -
+                                            (q.yv[b] - q.yv[a]) * (q.xv[c] - q.xv[e]));
+                    if (!(A > 0.0))
+                        return fail(ROEAM_E_ARG,
+                                    "grid %d: cell (%d, %d) has area %g <= 0 (vertices must turn counter-clockwise "
+                                    "from +i to +j)", k, I, J, A);
+                }
+        }
         for (int s = 0; s < 4; ++s)
             if (q.bc[s] < 0 || q.bc[s] > 3) return fail(ROEAM_E_ARG, "grid %d: bad boundary type on side %d", k, s);
         if ((q.bc[0] == ROEAM_BC_PERIODIC) != (q.bc[1] == ROEAM_BC_PERIODIC) ||

@@ -298,3 +298,44 @@ def test_classical_roe_time_step_rule():
     rate = oracle.OracleGrid(spec).max_rate(U)
     assert abs(rate - ref) <= 1e-14 * ref
     assert oracle.OracleGrid(W.with_params(spec, scheme=0)).max_rate(U) > 2 * ref
+
+
+# ----------------------------------------------------------------------------- cylinder grids
+def test_ogrid_area_and_closure():
+    """The O-grid of the Section 7.6 cylinder: total cell area equals the polygonal annulus
+    (ni/2) sin(2 pi/ni) (r_far^2 - 1) (closed form), and a uniform flow has zero residual in
+    every cell off the wall row (closed cells, bit-identical periodic seam, far field = free
+    stream)."""
+    spec, _ = W.cylinder_ogrid(ni=40, nj=24, mach=0.3, r_far=10.0)
+    g = oracle.OracleGrid(spec)
+    ones = W.prim_to_cons(np.ones((24, 40)), 0.0, 0.0, np.ones((24, 40)))
+    area = g.totals(ones)[0]
+    assert abs(area - 20 * math.sin(2 * math.pi / 40) * (100 - 1)) <= 1e-12 * area
+    U = W.free_stream(spec, 1.0, 0.3, 0.0, 1 / 1.4)
+    R = g.residual(U)
+    xv, yv = spec.xv, spec.yv
+    edge = lambda a, b: np.hypot(xv[a] - xv[b], yv[a] - yv[b])
+    perim = (edge((slice(None, -1), slice(None, -1)), (slice(None, -1), slice(1, None))) +
+             edge((slice(1, None), slice(None, -1)), (slice(1, None), slice(1, None))) +
+             edge((slice(None, -1), slice(None, -1)), (slice(1, None), slice(None, -1))) +
+             edge((slice(None, -1), slice(1, None)), (slice(1, None), slice(1, None))))
+    Vc = 0.5 * ((xv[1:, 1:] - xv[:-1, :-1]) * (yv[1:, :-1] - yv[:-1, 1:]) -
+                (yv[1:, 1:] - yv[:-1, :-1]) * (xv[1:, :-1] - xv[:-1, 1:]))
+    scale = np.max((1 / 1.4 + 0.09) * perim / Vc)    # |F| |S| / V bound of the face fluxes
+    assert np.max(np.abs(R[:, 1:])) <= 1e-13 * scale, np.max(np.abs(R[:, 1:])) / scale
+    assert np.max(np.abs(R[:, 0])) > 1e-6   # the wall does act
+
+
+@pytest.mark.parametrize("gen", ["ogrid", "blunt"])
+def test_cylinder_mirror_symmetry(gen):
+    """Both cylinder grids are symmetric about the x-axis with cell i mirrored to ni-1-i; the
+    residual of a mirror-symmetric state is mirror-symmetric (rho v odd)."""
+    if gen == "ogrid":
+        spec, U = W.cylinder_ogrid(ni=40, nj=20, mach=0.2, r_far=8.0)
+    else:
+        spec, U = W.cylinder_blunt(ni=40, nj=10, mach=3.0)
+        U = U * (1 + 0.1 * np.sin(np.linspace(0, 3, 10))[None, :, None] * np.array([1, 0, 0, 1])[:, None, None])
+    R = oracle.OracleGrid(spec).residual(U)
+    Rm = R[:, :, ::-1].copy()
+    Rm[2] *= -1
+    assert np.max(np.abs(R - Rm)) <= 1e-12 * np.max(np.abs(R))

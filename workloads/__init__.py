@@ -346,5 +346,63 @@ def warped_periodic(n: int = 32, amp: float = 0.1, seed: int = DEFAULT_SEED) -> 
     return GridSpec(ni=n, nj=n, dx=d, dy=d, xv=X + amp * d * s, yv=Y + amp * d * s)
 
 
+def cylinder_ogrid(ni: int = 100, nj: int = 72, mach: float = 0.01, r_far: float = 20.0,
+                   recon: int = RECON_FIRST, gamma: float = GAMMA) -> Tuple[GridSpec, np.ndarray]:
+    """Low-Mach inviscid flow past a unit cylinder (Section 7.6) on an O-grid of ni cells
+    around the circumference and nj cells out to r_far, radii growing geometrically (first
+    radial spacing about 2 pi / ni * 0.7). i runs clockwise from the upstream stagnation point
+    (theta = pi - 2 pi i / ni; periodic W/E, the seam column repeats column 0 bit for bit), j
+    outward: S is the cylinder wall, N the far field (the free stream imposed as INFLOW).
+    Free stream rho = 1, p = 1/gamma (c = 1), u = mach along +x. Vertices are absolute
+    coordinates (dx = dy = 0). Initial state: incompressible potential flow with Bernoulli
+    pressure and isentropic density, evaluated at the cell centres."""
+    q = r_far ** (1.0 / nj)
+    r = q ** np.arange(nj + 1, dtype=np.float64)
+    r[-1] = r_far
+    th = np.pi - 2.0 * np.pi * np.arange(ni + 1, dtype=np.float64) / ni
+    R, TH = np.meshgrid(r, th, indexing="ij")
+    xv = R * np.cos(TH)
+    yv = R * np.sin(TH)
+    xv[:, ni] = xv[:, 0]
+    yv[:, ni] = yv[:, 0]
+    p_inf = 1.0 / gamma
+    spec = GridSpec(ni=ni, nj=nj, dx=0.0, dy=0.0, bc=(PERIODIC, PERIODIC, WALL, INFLOW),
+                    inflow=(1.0, mach, 0.0, p_inf), xv=xv, yv=yv,
+                    params=SchemeParams(gamma=gamma, m_ref=mach, u_ref=mach, recon=recon))
+    xc, yc = spec.cell_centres()
+    rc2 = xc * xc + yc * yc
+    c2t = (xc * xc - yc * yc) / rc2          # cos 2 theta
+    s2t = 2.0 * xc * yc / rc2                # sin 2 theta
+    u = mach * (1.0 - c2t / rc2)
+    v = -mach * s2t / rc2
+    p = p_inf + 0.5 * (mach * mach - (u * u + v * v))
+    rho = (p / p_inf) ** (1.0 / gamma)
+    return spec, prim_to_cons(rho, u, v, p, gamma)
+
+
+def cylinder_blunt(ni: int = 160, nj: int = 20, mach: float = 20.0, recon: int = RECON_FIRST,
+                   gamma: float = GAMMA) -> Tuple[GridSpec, np.ndarray]:
+    """Hypersonic flow onto the front half of a unit cylinder (Section 7.5, carbuncle test):
+    ni cells around the half circle (theta from 3 pi / 2 down to pi / 2, so i runs clockwise
+    from the bottom shoulder over the stagnation point to the top), nj equal radial cells out
+    to r_out(phi) = 1.6 + 1.4 sin^2 phi (phi = angle from the stagnation line), outside the bow
+    shock at Mach 20. S: cylinder wall; N: supersonic free stream (INFLOW); W/E: supersonic
+    outflow (zero gradient). Free stream rho = 1, p = 1/gamma, u = mach along +x, imposed in
+    every cell at t = 0 (impulsive start)."""
+    th = 1.5 * np.pi - np.pi * np.arange(ni + 1, dtype=np.float64) / ni
+    phi = th - np.pi
+    r_out = 1.6 + 1.4 * np.sin(phi) ** 2
+    s = np.arange(nj + 1, dtype=np.float64) / nj
+    R = 1.0 + s[:, None] * (r_out[None, :] - 1.0)
+    xv = R * np.cos(th)[None, :]
+    yv = R * np.sin(th)[None, :]
+    p_inf = 1.0 / gamma
+    spec = GridSpec(ni=ni, nj=nj, dx=0.0, dy=0.0, bc=(OUTFLOW, OUTFLOW, WALL, INFLOW),
+                    inflow=(1.0, mach, 0.0, p_inf), xv=xv, yv=yv,
+                    params=SchemeParams(gamma=gamma, m_ref=min(mach, 1.0), u_ref=mach, recon=recon))
+    z = np.zeros((nj, ni))
+    return spec, prim_to_cons(z + 1.0, z + mach, z, z + p_inf, gamma)
+
+
 def with_params(spec: GridSpec, **kw) -> GridSpec:
     return replace(spec, params=replace(spec.params, **kw))
