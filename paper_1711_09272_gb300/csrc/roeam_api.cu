@@ -183,6 +183,8 @@ roeam_status upload_coef(roeam_grid *g)
         c.dy = T(G.dy);
         c.V = T(G.dx * G.dy);
         c.Vi = T(1.0 / (G.dx * G.dy));
+        c.idx = T(1.0 / G.dx);
+        c.idy = T(1.0 / G.dy);
         for (int s = 0; s < 4; ++s) c.inflow[s] = T(G.inflow[s]);
         c.harten = T(G.harten);
     }

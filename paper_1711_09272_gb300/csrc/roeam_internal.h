@@ -41,6 +41,7 @@ template <typename T>
 struct GridCoef {
     T g, gm1, gm1i, hgm1, mr2, rr_thr, eps2;   // gamma, gamma-1, 1/(gamma-1), (gamma-1)/2, M_ref^2, 1e-5 U_ref, eps2
     T dx, dy, V, Vi;                     // spacings (reference spacings if curvilinear), dx*dy, 1/(dx*dy)
+    T idx, idy;                          // 1/dx, 1/dy (Cartesian)
     T inflow[4];                         // rho, u, v, p of INFLOW sides
     T harten;                            // classical Roe: eps_lambda (0: no entropy fix)
 };

@@ -309,36 +309,48 @@ __device__ __forceinline__ CellGeom<T> cell_geom(T x00, T x10, T x01, T x11, T y
     return c;
 }
 
-// Largest dissipative signal speed normal to a face: |U| + max(c, c~/theta), Eqs. 99-101 on
-// the cell state (classical |U| + c when theta = 1).
-template <typename T> __device__ __forceinline__ T signal_speed(T Un, T c, T q2, T mr2)
+// Velocity, |q|^2 and pressure of a conserved state, with explicit rounding: the stage
+// epilogue's positivity check and the time-step rate share them.
+template <typename T> struct CellPrims { T ri, u, v, q2, p; };
+template <typename T>
+__device__ __forceinline__ CellPrims<T> cell_prims(T r, T ru, T rv, T rE, const GridCoef<T> &K)
 {
-    const T c2 = rmul(c, c);
-    const T th = vmin(vmax(mr2, q2 / c2), T(1));
-    if (th >= T(1)) return radd(vabs(Un), c);
-    const T om = rsub(T(1), th);
-    const T ct = rmul(T(0.5), sqrt(radd(rmul(rmul(T(4), c2), th), rmul(rmul(om, om), rmul(Un, Un)))));
-    return radd(vabs(Un), vmax(c, ct / th));
+    CellPrims<T> s;
+    s.ri = rcp(r);
+    s.u = rmul(ru, s.ri);
+    s.v = rmul(rv, s.ri);
+    s.q2 = radd(rmul(s.u, s.u), rmul(s.v, s.v));
+    s.p = rmul(K.gm1, rsub(rE, rmul(rmul(T(0.5), r), s.q2)));
+    return s;
 }
 
-// The rate sum_dir speed_dir |S_dir| / V of one cell, from its conserved state.
+// The rate sum_dir speed_dir |S_dir| / V of one cell (the time step is CFL / max rate). The
+// speed normal to a direction is |U| + max(c, c~/theta), with theta and c~ of Eqs. 99-101 on
+// the cell state: theta depends only on the cell's Mach number, so both directions share it
+// (classical |U| + c when theta = 1).
 template <bool CURV, typename T>
-__device__ __forceinline__ T cell_rate_cons(T r, T ru, T rv, T rE, const CellGeom<T> &cg, const GridCoef<T> &K)
+__device__ __forceinline__ T cell_rate(const CellPrims<T> &s, const CellGeom<T> &cg, const GridCoef<T> &K)
 {
-    const T ri = T(1) / r;
-    const T u = rmul(ru, ri), v = rmul(rv, ri);
-    const T q2 = radd(rmul(u, u), rmul(v, v));
-    const T p = rmul(K.gm1, rsub(rE, rmul(rmul(T(0.5), r), q2)));
-    const T c = sqrt(rmul(rmul(K.g, p), ri));
+    const T c2 = rmul(rmul(K.g, s.p), s.ri);
+    const T c = sqrt0(c2);
+    const T th = vmin(vmax(K.mr2, rmul(s.q2, rcp(c2))), T(1));
+    T Ux = s.u, Uy = s.v, lx = T(1), ly = T(1);
     if constexpr (CURV) {
-        const T lx = sqrt(radd(rmul(cg.Xx, cg.Xx), rmul(cg.Xy, cg.Xy)));
-        const T ly = sqrt(radd(rmul(cg.Yx, cg.Yx), rmul(cg.Yy, cg.Yy)));
-        const T sx = signal_speed(radd(rmul(u, cg.Xx), rmul(v, cg.Xy)) / lx, c, q2, K.mr2);
-        const T sy = signal_speed(radd(rmul(u, cg.Yx), rmul(v, cg.Yy)) / ly, c, q2, K.mr2);
-        return radd(rmul(sx, lx), rmul(sy, ly)) / cg.V;
-    } else {
-        return radd(signal_speed(u, c, q2, K.mr2) / K.dx, signal_speed(v, c, q2, K.mr2) / K.dy);
+        lx = sqrt0(radd(rmul(cg.Xx, cg.Xx), rmul(cg.Xy, cg.Xy)));
+        ly = sqrt0(radd(rmul(cg.Yx, cg.Yx), rmul(cg.Yy, cg.Yy)));
+        Ux = rmul(radd(rmul(s.u, cg.Xx), rmul(s.v, cg.Xy)), rcp(lx));
+        Uy = rmul(radd(rmul(s.u, cg.Yx), rmul(s.v, cg.Yy)), rcp(ly));
     }
+    T wx = c, wy = c;
+    if (th < T(1)) {
+        const T om = rsub(T(1), th), ith = rcp(th);
+        const T a = rmul(rmul(T(4), c2), th), o2 = rmul(om, om);
+        wx = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(Ux, Ux))))), ith));
+        wy = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(Uy, Uy))))), ith));
+    }
+    const T sx = radd(vabs(Ux), wx), sy = radd(vabs(Uy), wy);
+    if constexpr (CURV) return rmul(radd(rmul(sx, lx), rmul(sy, ly)), rcp(cg.V));
+    else return radd(rmul(sx, K.idx), rmul(sy, K.idy));
 }
 
 // Rate slots hold a non-negative rate as the bit pattern of the working precision (float bits
@@ -741,6 +753,9 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         const bool stage_mode = a.mode == MODE_STAGE;
         const bool combine = stage_mode && a.alpha != T(0);
 
+        // two rows per trip for the first-order kernels (measured faster; the reconstructing ones
+        // are not)
+#pragma unroll (MUSCL ? 1 : 2)
         for (int j = j0; j <= j1; ++j) {
             // U^n of row j (combined at iteration j+1), issued early
             T Un_next[4] = {T(0), T(0), T(0), T(0)};
@@ -867,14 +882,12 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                         }
                         for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = out[k];
                         if (!solid) {
-                            const T ri = rcp(out[0]);
-                            const T uu = out[1] * ri, vv = out[2] * ri;
-                            const T p = K.gm1 * (out[3] - T(0.5) * out[0] * (uu * uu + vv * vv));
-                            if (!(out[0] > T(0)) || !(p > T(0))) {
-                                const bool fin = isfinite((double)out[0]) && isfinite((double)p);
+                            const CellPrims<T> cp = cell_prims(out[0], out[1], out[2], out[3], K);
+                            if (!(out[0] > T(0)) || !(cp.p > T(0))) {
+                                const bool fin = isfinite((double)out[0]) && isfinite((double)cp.p);
                                 atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
                             } else if (a.want_rate) {
-                                my_rate = vmax(my_rate, cell_rate_cons<CURV>(out[0], out[1], out[2], out[3], cg, K));
+                                my_rate = vmax(my_rate, cell_rate<CURV>(cp, cg, K));
                             }
                         }
                     } else if (a.mode == MODE_RESIDUAL) {
@@ -972,7 +985,7 @@ __global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, const G
         } else {
             cg.Xx = K.dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = K.dx; cg.V = K.V;
         }
-        m = vmax(m, cell_rate_cons<CURV>(U[c], U[c + G.plane], U[c + 2 * G.plane], U[c + 3 * G.plane], cg, K));
+        m = vmax(m, cell_rate<CURV>(cell_prims(U[c], U[c + G.plane], U[c + 2 * G.plane], U[c + 3 * G.plane], K), cg, K));
     }
     m = block_max<256>(m, red);
     if (threadIdx.x == 0 && m > T(0)) atomicMax(rate + g, rate_bits(m));
