@@ -199,3 +199,79 @@ def test_low_mach_dissipation_roe_vs_roeam():
     assert keep[0, 0.01] > 0.6 and abs(keep[0, 0.01] - keep[0, 0.1]) < 0.02, keep
     assert loss[1, 0.01] > 5 * loss[0, 0.01] and loss[1, 0.01] > 2 * loss[1, 0.1], keep
     assert math.log10(ind[0, 0.1] / ind[0, 0.01]) >= 1.8, (ind, keep)
+
+
+def run_shock_case(spec, U, tend, prec=32, cfl=0.4, ramp=100):
+    """Steps to tend (CFL ramped from 0.02 over the first `ramp` steps, then chunks of at most
+    200 steps sized from the current dt; t is approximate to within one chunk's dt drift)."""
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        t, n = 0.0, 0
+        while t < tend:
+            c = min(cfl, 0.02 * 1.05 ** n) if n < ramp else cfl
+            dt = b.step(c, nsteps=1, want_dt=True)[0]
+            t += dt
+            n += 1
+            if n >= ramp:
+                k = min(int((tend - t) / dt * 0.95), 200)
+                if k > 1:
+                    t += k * b.step(c, nsteps=k, want_dt=True)[0]
+                    n += k
+        return b.get_state(0)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("case", ["corner", "dmr"])
+def test_shock_case_parity(case, prec):
+    """Full-grid one-step parity on the Section 7.3 corner (solid block, inflow, wall, outflow)
+    and the Section 7.4 wedge (curvilinear, walls) once the shocks have formed."""
+    spec, U = W.supersonic_corner(400) if case == "corner" else W.wedge_dmr(800, 200)
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        for n in range(60):
+            b.step(min(0.4, 0.02 * 1.05 ** n), nsteps=1)
+        U0 = b.get_state(0)
+        dt = b.step(0.4, nsteps=1, want_dt=True)[0]
+        U1 = b.get_state(0)
+    Uo, _ = oracle.OracleGrid(spec).step(U0, dt_fixed=dt)
+    fluid = np.ones(U0.shape[1:], bool) if spec.solid is None else spec.solid == 0
+    err = np.max(np.abs(U1 - Uo)[:, fluid].max(axis=1) / state_scale(Uo))
+    assert err <= (1e-12 if prec == 64 else 1e-5), err
+
+
+@pytest.mark.parametrize("variant,fails", [(dict(), False), (dict(eps1=1), False), (dict(scheme=1), True),
+                                           (dict(scheme=1, harten=0.2), True), (dict(xi_roe=1), True)])
+def test_supersonic_corner(variant, fails):
+    """Section 7.3 / Fig. 8: the Mach-5.09 shock diffracting over the 90-degree corner (400 x 400,
+    first order, FP32, t = 0.155). Roe-AM reaches the end with a positive state and the planar
+    part of the shock where a Mach-5.09 shock should be (x = 0.05 + 5.09 t); classical Roe, with
+    or without the entropy fix, and Roe-AM with xi = |U| (no velocity-positivity xi of Eq. 86) stop
+    on a non-positive state in the near-vacuum expansion at the corner."""
+    spec, U = W.supersonic_corner(400)
+    spec = W.with_params(spec, **variant)
+    if fails:
+        with pytest.raises(P().RoeamError) as e:
+            run_shock_case(spec, U, 0.155)
+        assert e.value.status in (4, 5)
+        return
+    rho = run_shock_case(spec, U, 0.155)[0]
+    fronts = [int(np.where(rho[j] > 2.0)[0].max()) for j in range(330, 400, 10)]
+    x_front = (np.mean(fronts) + 0.5) / 400
+    assert abs(x_front - (0.05 + 5.09 * 0.155)) < 0.02, fronts
+    assert max(fronts) - min(fronts) <= 2, fronts   # the planar part stays planar
+
+
+def test_double_mach_reflection_kinked_stem():
+    """Section 7.4 / Fig. 9: the Mach-10 shock reflected from the 30-degree wedge (800 x 200,
+    first order, FP32, t = 0.2). Classical Roe grows the kinked Mach stem: its foot runs ahead
+    along the wall (~37 cells) and the stem leans forward (41 cells over its lowest 20 rows, vs 19
+    for Roe-AM, close to a stem normal to the ramp); Roe-AM, with eps1 = 0 or 1, does not."""
+    def stem(variant):
+        spec, U = W.wedge_dmr(800, 200)
+        rho = run_shock_case(W.with_params(spec, **variant), U, 0.2)[0]
+        f = [int(np.where(rho[j] > 2.1)[0].max()) for j in (0, 20)]
+        return f[0], f[0] - f[1]
+    foot_roe, lean_roe = stem(dict(scheme=1))
+    for v in (dict(), dict(eps1=1)):
+        foot, lean = stem(v)
+        assert lean <= 25 and foot_roe - foot >= 20 and lean_roe >= 32, (foot, lean, foot_roe, lean_roe)

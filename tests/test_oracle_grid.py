@@ -51,6 +51,33 @@ def test_quirk_states_are_mach6_rankine_hugoniot():
     assert abs(u2 - W.QUIRK_POST[1]) < 1e-12
 
 
+@pytest.mark.parametrize("M,post,tol", [(5.09, "CORNER_POST", 2e-5), (10.0, "DMR_POST", 1e-12)])
+def test_corner_and_dmr_states_are_rankine_hugoniot(M, post, tol):
+    """The Section 7.3 state (printed to 6 digits) is the post-shock state of a Mach-5.09 shock
+    into still air (1.4, 0, 0, 1); the Section 7.4 one that of the Mach-10 shock."""
+    g, (rho1, _, _, p1) = 1.4, W.STILL_AIR
+    rho2 = rho1 * (g + 1) * M * M / ((g - 1) * M * M + 2)
+    p2 = p1 * (1 + 2 * g / (g + 1) * (M * M - 1))
+    u2 = M * (1 - rho1 / rho2)
+    ref = getattr(W, post)
+    for a, b in ((rho2, ref[0]), (u2, ref[1]), (p2, ref[3])):
+        assert abs(a - b) <= tol * abs(a), (a, b)
+
+
+def test_wedge_grid_geometry():
+    """The Section 7.4 wedge grid: flat wall up to the tip, then a 30-degree ramp; the cell areas
+    add up to the area between the lid and the piecewise-linear wall."""
+    spec, _ = W.wedge_dmr(80, 20, x_tip=0.5, ramp=3.0, height=2.8)
+    yb = spec.yv[0]
+    slope = np.diff(yb) / np.diff(spec.xv[0])
+    assert np.allclose(slope[spec.xv[0][1:] > 0.5 + 1e-9][1:], math.tan(math.pi / 6))
+    ones = W.prim_to_cons(np.ones((20, 80)), 0.0, 0.0, np.ones((20, 80)))
+    area = oracle.OracleGrid(spec).totals(ones)[0]
+    x = spec.xv[0]
+    exact = float(np.sum(np.diff(x) * (2.8 - 0.5 * (yb[1:] + yb[:-1]))))   # trapezoids under the lid
+    assert abs(area - exact) <= 1e-12 * exact
+
+
 def test_exact_riemann_textbook_values():
     """The exact Riemann helper reproduces published star states (Toro 2009, Table 4.2:
     Sod's problem and the left half of the blast wave, which is the Section 7.1.3 case)."""

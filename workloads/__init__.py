@@ -404,5 +404,52 @@ def cylinder_blunt(ni: int = 160, nj: int = 20, mach: float = 20.0, recon: int =
     return spec, prim_to_cons(z + 1.0, z + mach, z, z + p_inf, gamma)
 
 
+# Mach-5.09 and Mach-10 shocks into rho = 1.4, p = 1 (c = 1): post-shock (rho, u, v, p).
+CORNER_POST = (7.04108, 4.07794, 0.0, 30.05942)    # Section 7.3
+DMR_POST = (8.0, 8.25, 0.0, 116.5)                  # Mach 10 (Section 7.4)
+STILL_AIR = (1.4, 0.0, 0.0, 1.0)
+
+
+def supersonic_corner(n: int = 400, x_shock: float = 0.05, y_corner: float = 0.5,
+                      recon: int = RECON_FIRST) -> Tuple[GridSpec, np.ndarray]:
+    """Shock diffraction over a 90-degree corner (Section 7.3): [0,1]^2 with n x n cells, the
+    block x < x_shock, y < y_corner solid; a Mach-5.09 shock at x = x_shock above the corner
+    with the paper's post-shock state behind it. W: post-shock INFLOW; N: wall; E, S:
+    zero-gradient outflow."""
+    spec = GridSpec(ni=n, nj=n, dx=1.0 / n, dy=1.0 / n, bc=(INFLOW, OUTFLOW, OUTFLOW, WALL), inflow=CORNER_POST,
+                    params=SchemeParams(m_ref=1.0, u_ref=CORNER_POST[1], recon=recon))
+    xc, yc = spec.cell_centres()
+    spec.solid = ((xc < x_shock) & (yc < y_corner)).astype(np.uint8)
+    post = xc < x_shock
+    rho = np.where(post, CORNER_POST[0], STILL_AIR[0])
+    u = np.where(post, CORNER_POST[1], 0.0)
+    p = np.where(post, CORNER_POST[3], STILL_AIR[3])
+    return spec, prim_to_cons(rho, u, 0.0 * rho, p)
+
+
+def wedge_dmr(ni: int = 800, nj: int = 200, x_tip: float = 0.5, ramp: float = 3.0, height: float = 2.8,
+              recon: int = RECON_FIRST) -> Tuple[GridSpec, np.ndarray]:
+    """Double-Mach reflection (Section 7.4) in the wedge frame: a Mach-10 shock, normal to a flat
+    wall, meets a 30-degree ramp at x_tip, so that relative to the ramp it is inclined at 60
+    degrees (the usual rotated set-up). Curvilinear ni x nj grid: columns x uniform on
+    [0, x_tip + ramp cos 30], rows from the wall (flat, then the ramp) to a flat upper wall at
+    `height`. The shock starts 0.05 before the tip. W: post-shock INFLOW; E: outflow; S, N:
+    walls."""
+    L = x_tip + ramp * math.cos(math.pi / 6)
+    x = np.linspace(0.0, L, ni + 1)
+    yb = np.where(x > x_tip, (x - x_tip) * math.tan(math.pi / 6), 0.0)
+    s = np.arange(nj + 1, dtype=np.float64)[:, None] / nj
+    xv = np.broadcast_to(x[None, :], (nj + 1, ni + 1)).copy()
+    yv = yb[None, :] + s * (height - yb[None, :])
+    spec = GridSpec(ni=ni, nj=nj, dx=L / ni, dy=height / nj, bc=(INFLOW, OUTFLOW, WALL, WALL), inflow=DMR_POST,
+                    xv=xv, yv=yv, params=SchemeParams(m_ref=1.0, u_ref=DMR_POST[1], recon=recon))
+    xc, _ = spec.cell_centres()
+    post = xc < x_tip - 0.05
+    rho = np.where(post, DMR_POST[0], STILL_AIR[0])
+    u = np.where(post, DMR_POST[1], 0.0)
+    p = np.where(post, DMR_POST[3], STILL_AIR[3])
+    return spec, prim_to_cons(rho, u, 0.0 * rho, p)
+
+
 def with_params(spec: GridSpec, **kw) -> GridSpec:
     return replace(spec, params=replace(spec.params, **kw))
