@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "roeam_oracle.c")
+_SRC3 = os.path.join(_HERE, "roeam_oracle3.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS = {}
@@ -42,15 +43,27 @@ class OrcGrid(C.Structure):
                 ("prm", OrcParams)]
 
 
+class Orc3Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("m_ref", C.c_double), ("u_ref", C.c_double), ("eps2", C.c_double),
+                ("eps1", C.c_int), ("use_s1", C.c_int), ("xi_form", C.c_int), ("nscal", C.c_int)]
+
+
+class Orc3Grid(C.Structure):
+    _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int), ("bc", C.c_int * 6), ("inflow", C.c_double * 8),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("prm", Orc3Params)]
+
+
 def build(force: bool = False) -> Tuple[str, str]:
     """Compile the oracle (double and long double builds) into oracle/_build/."""
     os.makedirs(_BUILD, exist_ok=True)
     outs = []
     for tag, flags in (("", []), ("_ld", ["-DORC_LONG=1"])):
         out = os.path.join(_BUILD, f"liboracle{tag}.so")
-        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))
+        if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
             tmp = out + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *flags, "-o", tmp, _SRC, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *flags, "-o", tmp, _SRC, _SRC3,
+                                   "-lm"])
             os.replace(tmp, out)
         outs.append(out)
     return outs[0], outs[1]
@@ -75,6 +88,14 @@ def _lib(long_double: bool = False):
             getattr(lib, "orc_rk_step" + sfx).argtypes = [C.POINTER(OrcGrid), dp, C.c_double, C.c_double]
             getattr(lib, "orc_totals" + sfx).argtypes = [C.POINTER(OrcGrid), dp, dp]
             getattr(lib, "orc_detector" + sfx).argtypes = [C.POINTER(OrcGrid), dp, dp, dp]
+            getattr(lib, "orc3_face_flux" + sfx).argtypes = [C.POINTER(Orc3Params), C.c_int, dp, dp, dp, dp, dp]
+            getattr(lib, "orc3_residual" + sfx).argtypes = [C.POINTER(Orc3Grid), dp, dp]
+            getattr(lib, "orc3_max_rate" + sfx).restype = C.c_double
+            getattr(lib, "orc3_max_rate" + sfx).argtypes = [C.POINTER(Orc3Grid), dp]
+            getattr(lib, "orc3_rk_step" + sfx).restype = C.c_double
+            getattr(lib, "orc3_rk_step" + sfx).argtypes = [C.POINTER(Orc3Grid), dp, C.c_double, C.c_double]
+            getattr(lib, "orc3_totals" + sfx).argtypes = [C.POINTER(Orc3Grid), dp, dp]
+            getattr(lib, "orc3_detector" + sfx).argtypes = [C.POINTER(Orc3Grid), dp, C.c_int, dp]
             _LIBS[key] = (lib, sfx)
         return _LIBS[key]
 
@@ -195,3 +216,79 @@ def roe_average(WL, WR, gamma: float = 1.4) -> np.ndarray:
 
 def step_ref(spec, U, cfl=0.5, dt_fixed=0.0, nsteps=1, **variant):
     return OracleGrid(spec, **variant).step(U, cfl, dt_fixed, nsteps)
+
+
+# ----------------------------------------------------------------------------- 3D with scalars
+def make_params3(p=None, nscal: int = 0, **over) -> Orc3Params:
+    """3D oracle parameters from a workloads.SchemeParams (gamma, m_ref, u_ref, eps2, eps1,
+    use_s1, xi_form), with keyword overrides."""
+    d = dict(gamma=1.4, m_ref=0.5, u_ref=1.0, eps2=0.05, eps1=0, use_s1=1, xi_form=0)
+    if p is not None:
+        d.update({k: getattr(p, k) for k in d if hasattr(p, k)})
+    d.update(over)
+    return Orc3Params(float(d["gamma"]), float(d["m_ref"]), float(d["u_ref"]), float(d["eps2"]), int(d["eps1"]),
+                      int(d["use_s1"]), int(d["xi_form"]), int(nscal))
+
+
+def face_flux3(WL, WR, nrm, s1=None, nscal: int = 0, long_double: bool = False, **params) -> np.ndarray:
+    """Per-unit-area flux for n faces: W (n, 5 + nscal) = (rho, u, v, w, p, k..), unit normals
+    (n, 3) from L to R."""
+    nv = 5 + nscal
+    WL = np.ascontiguousarray(np.atleast_2d(WL), dtype=np.float64)
+    WR = np.ascontiguousarray(np.atleast_2d(WR), dtype=np.float64)
+    nrm = np.ascontiguousarray(np.atleast_2d(nrm), dtype=np.float64)
+    assert WL.shape[1] == nv and nrm.shape[1] == 3
+    n = WL.shape[0]
+    s = np.ones(n) if s1 is None else np.ascontiguousarray(np.broadcast_to(s1, (n,)), dtype=np.float64)
+    P = make_params3(None, nscal, **params)
+    F = np.empty((n, nv))
+    _fn("orc3_face_flux", long_double)(C.byref(P), n, _dptr(WL), _dptr(WR), _dptr(nrm), _dptr(s), _dptr(F))
+    return F
+
+
+class OracleGrid3:
+    """A workloads.GridSpec3 in the 3D oracle's layout."""
+
+    def __init__(self, spec, **over):
+        self.spec = spec
+        g = Orc3Grid()
+        g.ni, g.nj, g.nk = spec.ni, spec.nj, spec.nk
+        g.bc[:] = list(spec.bc)
+        inflow = list(spec.inflow) + [0.0] * (8 - len(spec.inflow))
+        g.inflow[:] = inflow
+        g.dx, g.dy, g.dz = spec.dx, spec.dy, spec.dz
+        g.prm = make_params3(spec.params, spec.nscal, **over)
+        self.g = g
+        self.nv = 5 + spec.nscal
+
+    def _u(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        assert U.shape == (self.nv, self.spec.nk, self.spec.nj, self.spec.ni), U.shape
+        return U
+
+    def residual(self, U, long_double: bool = False) -> np.ndarray:
+        U = self._u(U)
+        R = np.empty_like(U)
+        _fn("orc3_residual", long_double)(C.byref(self.g), _dptr(U), _dptr(R))
+        return R
+
+    def max_rate(self, U) -> float:
+        return _fn("orc3_max_rate")(C.byref(self.g), _dptr(self._u(U)))
+
+    def step(self, U, cfl: float = 0.5, dt_fixed: float = 0.0, nsteps: int = 1, long_double: bool = False):
+        U = self._u(U).copy()
+        dt = 0.0
+        for _ in range(nsteps):
+            dt = _fn("orc3_rk_step", long_double)(C.byref(self.g), _dptr(U), cfl, dt_fixed)
+        return U, dt
+
+    def totals(self, U) -> np.ndarray:
+        out = np.zeros(self.nv)
+        _fn("orc3_totals")(C.byref(self.g), _dptr(self._u(U)), _dptr(out))
+        return out
+
+    def detector(self, U, axis: int) -> np.ndarray:
+        U = self._u(U)
+        out = np.empty((self.spec.nk, self.spec.nj, self.spec.ni))
+        _fn("orc3_detector")(C.byref(self.g), _dptr(U), int(axis), _dptr(out))
+        return out

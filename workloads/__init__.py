@@ -115,7 +115,16 @@ class SplitMix64:
         return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
 
     def uniforms(self, n: int) -> np.ndarray:
-        return np.array([self.uniform() for _ in range(n)], dtype=np.float64)
+        """The next n uniforms, vectorised: output m is the mix of state + (m+1) * golden."""
+        if n <= 0:
+            return np.zeros(0)
+        with np.errstate(over="ignore"):
+            z = (np.uint64(self.state) + np.arange(1, n + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15))
+            self.state = int(z[-1])
+            z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            z = z ^ (z >> np.uint64(31))
+        return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -449,6 +458,127 @@ def wedge_dmr(ni: int = 800, nj: int = 200, x_tip: float = 0.5, ramp: float = 3.
     u = np.where(post, DMR_POST[1], 0.0)
     p = np.where(post, DMR_POST[3], STILL_AIR[3])
     return spec, prim_to_cons(rho, u, 0.0 * rho, p)
+
+
+# ----------------------------------------------------------------------------- 3D with scalars
+@dataclass
+class GridSpec3:
+    """One structured 3D Cartesian grid: ni x nj x nk cells of dx x dy x dz, boundary types
+    (W, E, S, N, B, T) = (-x, +x, -y, +y, -z, +z), nscal passive scalars. State arrays are
+    (5 + nscal, nk, nj, ni): rho, rho u, rho v, rho w, rho E, rho k_1.. . inflow is the
+    primitive (rho, u, v, w, p, k_1..) state imposed on INFLOW sides."""
+    ni: int
+    nj: int
+    nk: int
+    dx: float = 1.0
+    dy: float = 1.0
+    dz: float = 1.0
+    bc: Tuple[int, ...] = (PERIODIC,) * 6
+    inflow: Tuple[float, ...] = (1.0, 0.0, 0.0, 0.0, 1.0)
+    nscal: int = 0
+    params: SchemeParams = field(default_factory=SchemeParams)
+
+    @property
+    def ncells(self) -> int:
+        return self.ni * self.nj * self.nk
+
+    def cell_centres(self):
+        """(x, y, z) cell centres, each of shape (nk, nj, ni)."""
+        z, y, x = np.meshgrid((np.arange(self.nk) + 0.5) * self.dz, (np.arange(self.nj) + 0.5) * self.dy,
+                              (np.arange(self.ni) + 0.5) * self.dx, indexing="ij")
+        return x, y, z
+
+
+def prim_to_cons3(rho, u, v, w, p, scalars=(), gamma=GAMMA) -> np.ndarray:
+    """(rho, u, v, w, p, k..) -> (rho, rho u, rho v, rho w, rho E, rho k..)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    b = np.broadcast_to
+    u, v, w, p = (b(np.asarray(a, dtype=np.float64), rho.shape) for a in (u, v, w, p))
+    E = p / ((gamma - 1.0) * rho) + 0.5 * (u * u + v * v + w * w)
+    out = [rho, rho * u, rho * v, rho * w, rho * E] + [rho * b(np.asarray(k, dtype=np.float64), rho.shape)
+                                                          for k in scalars]
+    return np.stack(out)
+
+
+def cons_to_prim3(U: np.ndarray, gamma=GAMMA):
+    """(rho, u, v, w, p, [k..])."""
+    rho = U[0]
+    u, v, w = U[1] / rho, U[2] / rho, U[3] / rho
+    p = (gamma - 1.0) * (U[4] - 0.5 * rho * (u * u + v * v + w * w))
+    return (rho, u, v, w, p) + tuple(U[5 + s] / rho for s in range(U.shape[0] - 5))
+
+
+def random_rough_state3(spec: GridSpec3, seed: int = DEFAULT_SEED, mach: float = 1.0,
+                        jump: float = 0.5) -> np.ndarray:
+    """Cell-by-cell seeded random 3D state: rho, p log-uniform within exp(+-jump), velocity
+    components uniform in +-mach c, scalars uniform in [0, 1]."""
+    rng = SplitMix64(seed)
+    shape = (spec.nk, spec.nj, spec.ni)
+    g = spec.params.gamma
+    r = rng.uniforms((5 + spec.nscal) * spec.ncells).reshape((5 + spec.nscal,) + shape)
+    rho = np.exp(jump * (2 * r[0] - 1))
+    p = np.exp(jump * (2 * r[4] - 1))
+    c = np.sqrt(g * p / rho)
+    u, v, w = (mach * c * (2 * r[k] - 1) for k in (1, 2, 3))
+    return prim_to_cons3(rho, u, v, w, p, [r[5 + s] for s in range(spec.nscal)], gamma=g)
+
+
+def random_smooth_state3(spec: GridSpec3, seed: int = DEFAULT_SEED, mach: float = 0.5, amp: float = 0.2,
+                         modes: int = 3) -> np.ndarray:
+    """A seeded smooth periodic perturbation of a uniform flow: `modes` random Fourier modes in
+    each primitive variable; scalars smooth in [0, 1]."""
+    rng = SplitMix64(seed)
+    g = spec.params.gamma
+    x, y, z = spec.cell_centres()
+    L = (spec.ni * spec.dx, spec.nj * spec.dy, spec.nk * spec.dz)
+    cs = math.sqrt(g)
+    base = (1.0, mach * cs, -0.5 * mach * cs, 0.3 * mach * cs, 1.0) + (0.5,) * spec.nscal
+    out = []
+    for k in range(5 + spec.nscal):
+        f = np.full_like(x, base[k])
+        for _ in range(modes):
+            kk = [1 + int(rng.uniform() * 3) for _ in range(3)]
+            ph = 2 * math.pi * rng.uniform()
+            a = amp * (rng.uniform() - 0.5) * (mach * cs if k in (1, 2, 3) else 1.0)
+            f = f + a * np.sin(2 * math.pi * (kk[0] * x / L[0] + kk[1] * y / L[1] + kk[2] * z / L[2]) + ph)
+        out.append(f)
+    return prim_to_cons3(*out[:5], out[5:], gamma=g)
+
+
+def taylor_green3(n: int = 64, mach: float = 0.1, nscal: int = 1, recon: int = RECON_FIRST,
+                  gamma: float = GAMMA) -> Tuple[GridSpec3, np.ndarray]:
+    """Taylor-Green vortex on the periodic cube [0, 2 pi]^3 (n^3 cells): u = U0 sin x cos y cos z,
+    v = -U0 cos x sin y cos z, w = 0, p = p0 + (rho0 U0^2 / 16)(cos 2x + cos 2y)(cos 2z + 2),
+    rho0 = 1, U0 = 1, p0 = 1 / (gamma M^2); scalar k_s = (1 + sin(x + s) sin(y) sin(z)) / 2."""
+    h = 2 * math.pi / n
+    spec = GridSpec3(ni=n, nj=n, nk=n, dx=h, dy=h, dz=h, nscal=nscal,
+                     params=SchemeParams(gamma=gamma, m_ref=mach, u_ref=1.0, recon=recon))
+    x, y, z = spec.cell_centres()
+    p0 = 1.0 / (gamma * mach * mach)
+    u = np.sin(x) * np.cos(y) * np.cos(z)
+    v = -np.cos(x) * np.sin(y) * np.cos(z)
+    p = p0 + (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2) / 16.0
+    ks = [0.5 * (1 + np.sin(x + s) * np.sin(y) * np.sin(z)) for s in range(nscal)]
+    return spec, prim_to_cons3(np.ones_like(x), u, v, 0.0 * x, p, ks, gamma=gamma)
+
+
+def shock_tube3(name: str, n: int = 200, axis: int = 0, nt: int = 2, nscal: int = 1) -> Tuple[GridSpec3, np.ndarray]:
+    """A Section 7.1 tube along `axis` (0, 1, 2) of a 3D grid with nt cells in the two other
+    (periodic) directions, zero-gradient ends; scalar k = 1 on the left, 0 on the right (a
+    contact marker)."""
+    (rl, ul, pl), (rr, ur, pr), x0, _ = SHOCK_TUBES[name]
+    dims = [nt, nt, nt]
+    dims[axis] = n
+    bc = [PERIODIC] * 6
+    bc[2 * axis] = bc[2 * axis + 1] = OUTFLOW
+    spec = GridSpec3(ni=dims[0], nj=dims[1], nk=dims[2], dx=1.0 / n, dy=1.0 / n, dz=1.0 / n, bc=tuple(bc),
+                     nscal=nscal, params=SchemeParams(m_ref=1.0, u_ref=max(abs(ul), abs(ur), 1.0)))
+    c = spec.cell_centres()[axis]
+    left = c < x0
+    vel = [0.0 * c, 0.0 * c, 0.0 * c]
+    vel[axis] = np.where(left, ul, ur)
+    return spec, prim_to_cons3(np.where(left, rl, rr), *vel, np.where(left, pl, pr),
+                               [np.where(left, 1.0, 0.0)] * nscal)
 
 
 def with_params(spec: GridSpec, **kw) -> GridSpec:
