@@ -1,7 +1,8 @@
 """Compiles the CUDA library libroeam.so in-tree for sm_103a (GB300).
 
-The five translation units (host ABI, FP32 and FP64 kernels, FP32 and FP64 ablation-variant
-kernels) compile in parallel with nvcc and link into paper_1711_09272_gb300/_build/libroeam.so.
+The translation units (2D host ABI, FP32 and FP64 kernels, FP32 and FP64 ablation-variant
+kernels; 3D host ABI, FP32 and FP64 3D kernels) compile in parallel with nvcc and link into
+paper_1711_09272_gb300/_build/libroeam.so.
 """
 from __future__ import annotations
 
@@ -15,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libroeam.so")
-SOURCES = ["roeam_api.cu", "roeam_k32.cu", "roeam_k64.cu", "roeam_k32_abl.cu", "roeam_k64_abl.cu"]
+SOURCES = ["roeam_api.cu", "roeam_k32.cu", "roeam_k64.cu", "roeam_k32_abl.cu", "roeam_k64_abl.cu", "roeam3_api.cu",
+           "roeam3_k32.cu", "roeam3_k64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--prec-div=false", "--prec-sqrt=false",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -32,7 +34,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "roeam.h"), __file__]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", f) for f in
+                                                              os.listdir(os.path.join(ROOT, "include"))] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -477,6 +477,15 @@ roeam_status validate(int count, const roeam_grid_desc *d)
 
 }  // namespace
 
+namespace roeam {
+// Records a message for roeam_last_error() from the other host translation units.
+int record_error(int status, const char *msg)
+{
+    g_last_error = msg;
+    return status;
+}
+}  // namespace roeam
+
 extern "C" {
 
 const char *roeam_last_error(void) { return g_last_error.c_str(); }

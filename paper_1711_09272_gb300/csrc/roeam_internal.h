@@ -130,6 +130,9 @@ struct AblationLaunchers {
     static int stage_occupancy(int muscl, int curv);
 };
 
+// Sets the thread's roeam_last_error() message and returns `status` (host).
+int record_error(int status, const char *msg);
+
 // Fixed-order reduction of nblocks x 8 norm partials into out[8] (sum[4], max[4]).
 cudaError_t launch_reduce_partials(const double *partials, int nblocks, int width, double *out, cudaStream_t s);
 

@@ -25,7 +25,10 @@ ROEAM_NORM_L2, ROEAM_NORM_LINF = 0, 1
 EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual",
            "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
            "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
-           "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc"]
+           "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc",
+           "roeam3_create_grid", "roeam3_destroy_grid", "roeam3_set_state", "roeam3_get_state",
+           "roeam3_flux_residual", "roeam3_rk_step", "roeam3_conserved_totals", "roeam3_check",
+           "roeam3_launch_count"]
 
 
 class RoeamError(RuntimeError):
@@ -45,6 +48,12 @@ class roeam_grid_desc(C.Structure):
     _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("bc", C.c_int * 4), ("inflow", C.c_double * 4),
                 ("xv", C.POINTER(C.c_double)), ("yv", C.POINTER(C.c_double)), ("dx", C.c_double),
                 ("dy", C.c_double), ("solid", C.POINTER(C.c_uint8)), ("p", roeam_params)]
+
+
+class roeam3_grid_desc(C.Structure):
+    _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int), ("bc", C.c_int * 6), ("inflow", C.c_double * 8),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("nscal", C.c_int),
+                ("reserved_", C.c_int), ("p", roeam_params)]
 
 
 _lib = None
@@ -81,9 +90,22 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_set_tile_config.argtypes = [vp, C.c_int]
     lib.roeam_autotune.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
     lib.roeam_flux_residual_noalloc.argtypes = [vp, C.c_int, vp]
+    lib.roeam3_create_grid.argtypes = [C.c_int, C.POINTER(roeam3_grid_desc), C.c_int, vp, C.POINTER(vp)]
+    lib.roeam3_destroy_grid.argtypes = [vp]
+    lib.roeam3_destroy_grid.restype = None
+    lib.roeam3_set_state.argtypes = [vp, C.c_int, vp]
+    lib.roeam3_get_state.argtypes = [vp, C.c_int, vp]
+    lib.roeam3_flux_residual.argtypes = [vp, C.c_int, vp]
+    lib.roeam3_rk_step.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp]
+    lib.roeam3_conserved_totals.argtypes = [vp, C.c_int, dp]
+    lib.roeam3_check.argtypes = [vp]
+    lib.roeam3_launch_count.argtypes = [vp]
+    lib.roeam3_launch_count.restype = C.c_ulonglong
     for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
-                 "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc"):
+                 "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam3_create_grid",
+                 "roeam3_set_state", "roeam3_get_state", "roeam3_flux_residual", "roeam3_rk_step",
+                 "roeam3_conserved_totals", "roeam3_check"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -302,3 +324,137 @@ class Batch:
     @property
     def launches(self) -> int:
         return roeam_launch_count(self.handle)
+
+
+# ----------------------------------------------------------------------------- 3D (include/roeam3.h)
+def roeam3_create_grid(descs: Sequence[roeam3_grid_desc], device: int = 0, cuda_stream: int = 0) -> int:
+    lib = load_library()
+    arr = (roeam3_grid_desc * len(descs))(*descs)
+    h = C.c_void_p()
+    _check(lib.roeam3_create_grid(len(descs), arr, device, C.c_void_p(cuda_stream or None), C.byref(h)))
+    return h.value
+
+
+def roeam3_destroy_grid(h: int) -> None:
+    load_library().roeam3_destroy_grid(C.c_void_p(h))
+
+
+def roeam3_set_state(h: int, grid_idx: int, cons) -> None:
+    _check(load_library().roeam3_set_state(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(cons))))
+
+
+def roeam3_get_state(h: int, grid_idx: int, out) -> None:
+    _check(load_library().roeam3_get_state(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(out))))
+
+
+def roeam3_flux_residual(h: int, grid_idx: int, out=None) -> None:
+    _check(load_library().roeam3_flux_residual(C.c_void_p(h), grid_idx,
+                                               C.c_void_p(_ptr(out) if out is not None else None)))
+
+
+def roeam3_rk_step(h: int, cfl: float, dt_fixed: float, nsteps: int, dt_last=None) -> None:
+    _check(load_library().roeam3_rk_step(C.c_void_p(h), cfl, dt_fixed, nsteps,
+                                         C.c_void_p(_ptr(dt_last) if dt_last is not None else None)))
+
+
+def roeam3_conserved_totals(h: int, grid_idx: int, nv: int) -> np.ndarray:
+    out = np.zeros(nv)
+    _check(load_library().roeam3_conserved_totals(C.c_void_p(h), grid_idx, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def roeam3_check(h: int) -> None:
+    _check(load_library().roeam3_check(C.c_void_p(h)))
+
+
+def roeam3_launch_count(h: int) -> int:
+    return int(load_library().roeam3_launch_count(C.c_void_p(h)))
+
+
+def make_desc3(spec, precision: int = 64) -> roeam3_grid_desc:
+    """Descriptor from any object with the fields of workloads.GridSpec3."""
+    d = roeam3_grid_desc()
+    d.ni, d.nj, d.nk = int(spec.ni), int(spec.nj), int(spec.nk)
+    d.bc[:] = [int(b) for b in spec.bc]
+    inflow = [float(x) for x in spec.inflow] + [0.0] * (8 - len(spec.inflow))
+    d.inflow[:] = inflow[:8]
+    d.dx, d.dy, d.dz = float(spec.dx), float(spec.dy), float(spec.dz)
+    d.nscal = int(spec.nscal)
+    p = spec.params
+    d.p = roeam_params(p.gamma, p.m_ref, p.u_ref, p.eps2, int(p.eps1), int(p.use_s1), int(p.recon),
+                       int(p.xi_form), int(precision), 0, 0, 0, 0, 0, 0.0)
+    return d
+
+
+class Batch3:
+    """Owns a libroeam 3D handle for a list of workloads.GridSpec3-like specs."""
+
+    def __init__(self, specs, precision: int = 64, device: int = 0, cuda_stream: int = 0):
+        if not isinstance(specs, (list, tuple)):
+            specs = [specs]
+        self.specs = list(specs)
+        self.handle = roeam3_create_grid([make_desc3(s, precision) for s in self.specs], device, cuda_stream)
+        self.precision = precision
+        self.nv = 5 + self.specs[0].nscal
+        sizes = [self.nv * s.ni * s.nj * s.nk for s in self.specs]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+    def close(self):
+        if self.handle:
+            roeam3_destroy_grid(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _shape(self, idx):
+        s = self.specs[idx]
+        return (self.nv, s.nk, s.nj, s.ni)
+
+    def set_state(self, U, grid_idx: int = 0):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        assert U.shape == self._shape(grid_idx), (U.shape, self._shape(grid_idx))
+        roeam3_set_state(self.handle, grid_idx, U)
+
+    def set_states(self, Us):
+        packed = np.concatenate([np.ascontiguousarray(U, dtype=np.float64).ravel() for U in Us])
+        roeam3_set_state(self.handle, -1, packed)
+
+    def get_state(self, grid_idx: int = 0) -> np.ndarray:
+        out = np.empty(self._shape(grid_idx))
+        roeam3_get_state(self.handle, grid_idx, out)
+        return out
+
+    def get_states(self):
+        packed = np.empty(int(self.offsets[-1]))
+        roeam3_get_state(self.handle, -1, packed)
+        return [packed[self.offsets[k]:self.offsets[k + 1]].reshape(self._shape(k)) for k in range(len(self.specs))]
+
+    def residual(self, grid_idx: int = 0) -> np.ndarray:
+        out = np.empty(self._shape(grid_idx))
+        roeam3_flux_residual(self.handle, grid_idx, out)
+        return out
+
+    def step(self, cfl: float = 0.5, dt_fixed: float = 0.0, nsteps: int = 1, want_dt: bool = False):
+        dt = np.zeros(len(self.specs)) if want_dt else None
+        roeam3_rk_step(self.handle, cfl, dt_fixed, nsteps, dt)
+        return dt
+
+    def totals(self, grid_idx: int = 0) -> np.ndarray:
+        return roeam3_conserved_totals(self.handle, grid_idx, self.nv)
+
+    def check(self):
+        roeam3_check(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return roeam3_launch_count(self.handle)

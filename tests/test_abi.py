@@ -1,5 +1,5 @@
-"""The C-ABI library builds, loads and exports every entry point include/roeam.h declares
-(no compute calls: this runs without a GPU)."""
+"""The C-ABI library builds, loads and exports every entry point include/roeam.h and
+include/roeam3.h declare (no compute calls: this runs without a GPU)."""
 import os
 import re
 
@@ -9,9 +9,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "roeam.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(roeam_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in ("roeam.h", "roeam3.h"):
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(roeam3?_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_library_builds_and_exports_header_symbols():
