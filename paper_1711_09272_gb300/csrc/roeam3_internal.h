@@ -34,7 +34,10 @@ struct GridCoef3 {
 
 // Work-unit shape of the 3D stage kernel: a CTA of TY3 warps covers 32 columns (30 written)
 // by TY3 rows (TY3 - 2 written) and marches along z over a segment of planes.
-constexpr int TY3 = 8;
+#ifndef ROEAM_TY3
+#define ROEAM_TY3 8
+#endif
+constexpr int TY3 = ROEAM_TY3;
 constexpr int TILE3_X = 30, TILE3_Y = TY3 - 2;
 
 template <typename T>

@@ -224,8 +224,9 @@ template <typename T, int NS> struct Smem3 {
     static __host__ __device__ constexpr size_t bytes() { return sizeof(T) * 2 * (size_t)PER; }
 };
 
+// FP32 with 8-warp CTAs: two CTAs per SM (128 registers).
 template <typename T, int NS>
-__global__ void __launch_bounds__(32 * TY3) stage3_kernel(const StageArgs3<T> a)
+__global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1) stage3_kernel(const StageArgs3<T> a)
 {
     using SM = Smem3<T, NS>;
     constexpr int NV = 5 + NS, NC = SM::NC;
@@ -357,10 +358,15 @@ __global__ void __launch_bounds__(32 * TY3) stage3_kernel(const StageArgs3<T> a)
             Wl.Mq = shup(W0.Mq, 1);
 #pragma unroll
             for (int s = 0; s < NS; ++s) Wl.k[s] = shup(W0.k[s], 1);
+            // (the halo rows need none of their faces but the top row's south face)
             T Fw[NV], Fs[NV], Fb[NV];
-            face3<T, NS>(Wl, W0, 0, s1x, K.ax, K, eps1, xi_form, Fw);
-            face3<T, NS>(S, W0, 1, s1y, K.ay, K, eps1, xi_form, Fs);
-            face3<T, NS>(Wm, W0, 2, s1z, K.az, K, eps1, xi_form, Fb);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Fw[v] = Fs[v] = Fb[v] = T(0);
+            if (wy > 0) face3<T, NS>(S, W0, 1, s1y, K.ay, K, eps1, xi_form, Fs);
+            if (wy > 0 && wy < TY3 - 1) {
+                face3<T, NS>(Wl, W0, 0, s1x, K.ax, K, eps1, xi_form, Fw);
+                face3<T, NS>(Wm, W0, 2, s1z, K.az, K, eps1, xi_form, Fb);
+            }
 
             // the north neighbour's south flux
 #pragma unroll
