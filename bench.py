@@ -227,6 +227,53 @@ def warped_step_speed(P, torch, steps=20):
             "hbm_frac": v * (128.0 / 3 + 8) / peak, "peak_gbs": peak, "peak_kind": kind}
 
 
+def three_d_speed(P, torch, n=256, nscal=1, steps=20):
+    """The 3D path (include/roeam3.h): Taylor-Green vortex on n^3 cells, FP32, one passive
+    scalar, first order. Algorithmic bytes per cell and stage: (5 + nscal) 4-byte variables read
+    once and written once, plus the U^n read in stages 2-3, i.e. 8/3 x 4 (5 + nscal)."""
+    spec, U = W.taylor_green3(n, mach=0.1, nscal=nscal)
+    stream = torch.cuda.current_stream()
+    with P.Batch3([spec], precision=32, cuda_stream=stream.cuda_stream) as b:
+        b.set_state(U, 0)
+        b.step(0.5, nsteps=3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(0.5, nsteps=steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.check()
+        ms = e0.elapsed_time(e1) / steps
+    v = spec.ncells * 3 / (ms * 1e-3) / 1e9
+    bpc = 8.0 / 3.0 * 4 * (5 + nscal)
+    peak, kind = peaks()
+    return {"workload": f"3D Taylor-Green vortex {n}^3 periodic, M = 0.1, {nscal} passive scalar(s), FP32, first order",
+            "gcell_updates_per_s_per_stage": v, "ms_per_step": ms, "bytes_per_cell_stage": bpc,
+            "hbm_frac": v * bpc / peak, "peak_gbs": peak, "peak_kind": kind}
+
+
+def ablation_speed(P, torch, count=512, steps=50):
+    """The ablation-variant kernels (every face on the scalar path) on the benchmark batch with
+    the classical Roe flux (Eq. 7 with Eqs. 8-12), FP32, first order."""
+    specs, states = W.batch(count)
+    specs = [W.with_params(s, scheme=1) for s in specs]
+    ncells = sum(s.ncells for s in specs)
+    stream = torch.cuda.current_stream()
+    with P.Batch(specs, precision=32, cuda_stream=stream.cuda_stream) as b:
+        b.set_states(states)
+        b.step(0.5, nsteps=3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(0.5, nsteps=steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.check()
+        ms = e0.elapsed_time(e1) / steps
+    return {"workload": f"the {count}-grid batch with the classical Roe flux (ablation kernels), FP32, first order",
+            "gcell_updates_per_s_per_stage": ncells * 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms}
+
+
 def _oracle_worker(job):
     """One host process of the all-cores CPU baseline: steps grids w, w + P, w + 2P, ... of the
     seeded batch with the oracle for `budget` seconds of wall time; returns the cell-stages."""
@@ -410,6 +457,8 @@ def run_ours(args):
         if world == 1 and not args.no_extra:
             line["precision_comparison"] = precision_comparison(P, torch)
             line["curvilinear"] = warped_step_speed(P, torch)
+            line["three_d"] = three_d_speed(P, torch)
+            line["ablation_roe"] = ablation_speed(P, torch)
         print(json.dumps(line), flush=True)
     b.close()
     if world > 1:

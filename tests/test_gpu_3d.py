@@ -169,3 +169,28 @@ def test_shock_tube_along_each_axis(axis):
     # the exact Riemann solution), smeared over a few cells at first order
     xk = (np.argmax(k < 0.5) + 0.5) / 100
     assert abs(xk - 0.573) < 0.06, xk
+
+
+def test_full_size_sampled_parity_3d():
+    """The 3D measurement workload (Taylor-Green vortex, 256^3 cells, one scalar, FP32) after 20
+    steps: sampled cells of step 21 recomputed by the oracle on a 17^3 window around each (the
+    window's cut faces lie 8 cells away, beyond the 3 stages x 2-cell reach of a step)."""
+    n, R = 256, 8
+    spec, U = W.taylor_green3(n, mach=0.1, nscal=1)
+    with P().Batch3([spec], precision=32) as b:
+        b.set_state(U, 0)
+        b.step(0.5, nsteps=20)
+        U0 = b.get_state(0)
+        dt = b.step(0.5, nsteps=1, want_dt=True)[0]
+        U1 = b.get_state(0)
+    sc = scale3(U0)
+    rng = W.SplitMix64(3)
+    for _ in range(8):
+        i, j, k = (int(rng.uniform() * n) for _ in range(3))
+        idx = [np.arange(c - R, c + R + 1) % n for c in (k, j, i)]
+        Uw = U0[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+        sub = W.GridSpec3(ni=2 * R + 1, nj=2 * R + 1, nk=2 * R + 1, dx=spec.dx, dy=spec.dy, dz=spec.dz,
+                          bc=(W.OUTFLOW,) * 6, nscal=1, params=spec.params)
+        Uo, _ = oracle.OracleGrid3(sub).step(Uw, dt_fixed=dt)
+        err = np.max(np.abs(Uo[:, R, R, R] - U1[:, k, j, i]) / sc)
+        assert err <= 1e-5, (i, j, k, err)
