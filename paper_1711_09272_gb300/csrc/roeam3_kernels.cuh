@@ -75,10 +75,11 @@ __device__ __forceinline__ void finish3(const Pend3<T, NS> &p, bool inflow_xy, i
     derive3(c, K);
 }
 
-// One side of a face in the face frame: normal velocity un, tangential ut, uw.
-template <typename T, int NS> struct FS3 {
-    T r, un, ut, uw, p, c2, H, sr, Mq;
-    T k[NS > 0 ? NS : 1];
+// One side of a face in the face frame: normal velocity un, tangential ut, uw. V is the
+// working precision, or V2 for two faces evaluated together in packed FP32.
+template <typename V, int NS> struct FS3 {
+    V r, un, ut, uw, p, c2, H, sr, Mq;
+    V k[NS > 0 ? NS : 1];
 };
 
 template <typename T, int NS>
@@ -94,71 +95,84 @@ __device__ __forceinline__ FS3<T, NS> side3(const C3<T, NS> &c, int axis)
     return s;
 }
 
+// The sides of an x-face (component x) and a y-face (component y) packed together.
+template <int NS>
+__device__ __forceinline__ FS3<V2, NS> side3_xy(const C3<float, NS> &cx, const C3<float, NS> &cy)
+{
+    FS3<V2, NS> s;
+    s.r = mk2(cx.r, cy.r); s.p = mk2(cx.p, cy.p); s.c2 = mk2(cx.c2, cy.c2); s.H = mk2(cx.H, cy.H);
+    s.sr = mk2(cx.sr, cy.sr); s.Mq = mk2(cx.Mq, cy.Mq);
+    s.un = mk2(cx.u, cy.v); s.ut = mk2(cx.v, cy.u); s.uw = mk2(cx.w, cy.w);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) s.k[q] = mk2(cx.k[q], cy.k[q]);
+    return s;
+}
+
 // Twice the Roe-AM flux per unit area in the face frame (mass, normal momentum, the two
 // tangential momenta, energy, scalars): Section 6.2 term by term as in roeam_flux2, with the
 // w rows and Eq. 85's scalar rows; the rotated-Riemann estimate of Eqs. 103-109 in 3D
 // (n2 the unit part of n perpendicular to n1, so |a2 U2| = |U - a1 U1|).
-template <typename T, int NS>
-__device__ __forceinline__ void roeam_flux3(const FS3<T, NS> &L, const FS3<T, NS> &R, T s1, const GridCoef3<T> &K,
-                                            int eps1, int xi_form, T F[5 + NS])
+template <typename V, typename S, int NS>
+__device__ __forceinline__ void roeam_flux3(const FS3<V, NS> &L, const FS3<V, NS> &R, V s1, const GridCoef3<S> &K,
+                                            int eps1, int xi_form, V F[5 + NS])
 {
-    const T zero = T(0), one = T(1), half = T(0.5);
-    const T mL = L.r * L.un, mR = R.r * R.un;
-    const T F0c = mL + mR;
-    const T F1c = vfma(mL, L.un, vfma(mR, R.un, L.p + R.p));
-    const T F2c = vfma(mL, L.ut, mR * R.ut);
-    const T F3c = vfma(mL, L.uw, mR * R.uw);
-    const T F4c = vfma(mL, L.H, mR * R.H);
+    const V zero = splat<V>(0), one = splat<V>(1), half = splat<V>(S(0.5));
+    const V mL = L.r * L.un, mR = R.r * R.un;
+    const V F0c = mL + mR;
+    const V F1c = vfma(mL, L.un, vfma(mR, R.un, L.p + R.p));
+    const V F2c = vfma(mL, L.ut, mR * R.ut);
+    const V F3c = vfma(mL, L.uw, mR * R.uw);
+    const V F4c = vfma(mL, L.H, mR * R.H);
 
-    const T w = rcp(L.sr + R.sr);
-    const T rh = L.sr * R.sr;
-    const T uh = vfma(L.sr, L.un, R.sr * R.un) * w;
-    const T vh = vfma(L.sr, L.ut, R.sr * R.ut) * w;
-    const T wh = vfma(L.sr, L.uw, R.sr * R.uw) * w;
-    const T Hh = vfma(L.sr, L.H, R.sr * R.H) * w;
-    const T du = R.un - L.un, dv = R.ut - L.ut, dw = R.uw - L.uw;
-    const T dq2 = vfma(du, du, vfma(dv, dv, dw * dw));
-    const T c2h = vfma(vfma(L.sr, L.c2, R.sr * R.c2), w, K.hgm1 * rh * w * w * dq2);
-    const T chi = rsq(c2h);
-    const T ch = c2h * chi;
-    const T aU = vabs(uh);
+    const V w = rcp(L.sr + R.sr);
+    const V rh = L.sr * R.sr;
+    const V uh = vfma(L.sr, L.un, R.sr * R.un) * w;
+    const V vh = vfma(L.sr, L.ut, R.sr * R.ut) * w;
+    const V wh = vfma(L.sr, L.uw, R.sr * R.uw) * w;
+    const V Hh = vfma(L.sr, L.H, R.sr * R.H) * w;
+    const V du = R.un - L.un, dv = R.ut - L.ut, dw = R.uw - L.uw;
+    const V dq2 = vfma(du, du, vfma(dv, dv, dw * dw));
+    const V c2h = vfma(vfma(L.sr, L.c2, R.sr * R.c2), w, splat<V>(K.hgm1) * rh * w * w * dq2);
+    const V chi = rsq(c2h);
+    const V ch = c2h * chi;
+    const V aU = vabs(uh);
 
-    const T M = half * (L.Mq + R.Mq);
-    const T Mb = aU * chi;
-    const T fM = fmach(M), fMb = fmach(Mb);
-    const T fM8 = pow8(fM), fMb8 = pow8(fMb);
-    const T dp = R.p - L.p;
+    const V M = half * (L.Mq + R.Mq);
+    const V Mb = aU * chi;
+    const V fM = fmach(M), fMb = fmach(Mb);
+    const V fM8 = pow8(fM), fMb8 = pow8(fMb);
+    const V dp = R.p - L.p;
 
-    const T br = aU < ch ? T(2) : (aU == ch ? one : zero);
-    const T Up = du > zero ? vmax(vfma(T(-0.25) * fMb * br, du, aU), zero) : aU;
+    const V br = sel(lt(aU, ch), splat<V>(2), sel(eq(aU, ch), one, zero));
+    const V Up = sel(gt(du, zero), vmax(vfma(splat<V>(S(-0.25)) * fMb * br, du, aU), zero), aU);
 
-    const T xfac = xi_form ? one : one - fMb8;
-    T xi = vmax(vfma(xfac * half, du, vabs(half * (L.un + R.un))), zero);
+    const V xfac = xi_form ? one : one - fMb8;
+    V xi = vmax(vfma(xfac * half, du, vabs(half * (L.un + R.un))), zero);
     if (eps1) {
-        const T dq = sqrt0(dq2);
-        const bool big = dq >= K.rr_thr;
-        const T dqi = rcp(big ? dq : one);
-        const T n1x = big ? du * dqi : one;
-        const T U1 = big ? vfma(du, uh, vfma(dv, vh, dw * wh)) * dqi : uh;
-        const T frr = vabs(n1x * U1) + vabs(vfma(-n1x, U1, uh));
-        xi = vmax(xi, (one - fMb8) * fM8 * vmin(K.eps2 * ch, frr));
+        const V dq = sqrt0(dq2);
+        const auto big = ge(dq, splat<V>(K.rr_thr));
+        const V dqi = rcp(sel(big, dq, one));
+        const V n1x = sel(big, du * dqi, one);
+        const V U1 = sel(big, vfma(du, uh, vfma(dv, vh, dw * wh)) * dqi, uh);
+        const V frr = vabs(n1x * U1) + vabs(vfma(-n1x, U1, uh));
+        xi = vmax(xi, (one - fMb8) * fM8 * vmin(splat<V>(K.eps2) * ch, frr));
     }
 
-    const T mn = vmin(Up, ch);
-    const T smc = vcopysign(mn, uh) * chi;
-    const T pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmax(ch - Up, zero) * rh * du);
-    const T th = vmin(vmax(K.mr2, M * M), one);
-    const T om = one - th;
-    const T X = vfma(T(4) * c2h, th, om * om * uh * uh);
-    const T rX = rsq(X);
-    const T ct = half * X * rX;
-    const T Ut = half * (one + th) * uh;
-    const T term = vfma(om, Up - aU * rX * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
-    const T A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
-    const T dUu = half * smc * du;
+    const V mn = vmin(Up, ch);
+    const V smc = vcopysign(mn, uh) * chi;
+    const V pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmax(ch - Up, zero) * rh * du);
+    const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
+    const V om = one - th;
+    const V X = vfma(splat<V>(4) * c2h, th, om * om * uh * uh);
+    const V rX = rsq(X);
+    const V ct = half * X * rX;
+    const V Ut = half * (one + th) * uh;
+    const V term = vfma(om, Up - aU * rX * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
+    const V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
+    const V dUu = half * smc * du;
 
-    const T QL2 = L.r * L.ut, QR2 = R.r * R.ut, QL3 = L.r * L.uw, QR3 = R.r * R.uw;
-    const T QL4 = L.r * L.H, QR4 = R.r * R.H;
+    const V QL2 = L.r * L.ut, QR2 = R.r * R.ut, QL3 = L.r * L.uw, QR3 = R.r * R.uw;
+    const V QL4 = L.r * L.H, QR4 = R.r * R.H;
     F[0] = F0c - vfma(xi, R.r - L.r, vfma(dUu, R.r + L.r, A));
     F[1] = F1c - vfma(xi, mR - mL, vfma(dUu, mR + mL, vfma(A, uh, pp)));
     F[2] = F2c - vfma(xi, QR2 - QL2, vfma(dUu, QR2 + QL2, A * vh));
@@ -166,8 +180,8 @@ __device__ __forceinline__ void roeam_flux3(const FS3<T, NS> &L, const FS3<T, NS
     F[4] = F4c - vfma(xi, QR4 - QL4, vfma(dUu, QR4 + QL4, A * Hh));
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const T QLk = L.r * L.k[s], QRk = R.r * R.k[s];
-        const T kh = vfma(L.sr, L.k[s], R.sr * R.k[s]) * w;
+        const V QLk = L.r * L.k[s], QRk = R.r * R.k[s];
+        const V kh = vfma(L.sr, L.k[s], R.sr * R.k[s]) * w;
         F[5 + s] = vfma(mL, L.k[s], mR * R.k[s]) - vfma(xi, QRk - QLk, vfma(dUu, QRk + QLk, A * kh));
     }
 }
@@ -178,7 +192,7 @@ __device__ __forceinline__ void face3(const C3<T, NS> &a, const C3<T, NS> &b, in
                                       const GridCoef3<T> &K, int eps1, int xi_form, T F[5 + NS])
 {
     T G2[5 + NS];
-    roeam_flux3<T, NS>(side3(a, axis), side3(b, axis), s1, K, eps1, xi_form, G2);
+    roeam_flux3<T, T, NS>(side3(a, axis), side3(b, axis), s1, K, eps1, xi_form, G2);
     const T h = T(0.5) * area;
     F[0] = h * G2[0];
     F[4] = h * G2[4];
@@ -187,6 +201,23 @@ __device__ __forceinline__ void face3(const C3<T, NS> &a, const C3<T, NS> &b, in
     else { F[1] = h * G2[2]; F[2] = h * G2[3]; F[3] = h * G2[1]; }
 #pragma unroll
     for (int s = 0; s < NS; ++s) F[5 + s] = h * G2[5 + s];
+}
+
+// The x-face (Lx | B) and the y-face (Ly | B) of one cell together in packed FP32.
+template <int NS>
+__device__ __forceinline__ void faces3_xy(const C3<float, NS> &Lx, const C3<float, NS> &Ly, const C3<float, NS> &B,
+                                          float s1x, float s1y, const GridCoef3<float> &K, int eps1, int xi_form,
+                                          float Fx[5 + NS], float Fy[5 + NS])
+{
+    V2 G2[5 + NS];
+    roeam_flux3<V2, float, NS>(side3_xy(Lx, Ly), side3_xy(B, B), mk2(s1x, s1y), K, eps1, xi_form, G2);
+    const float hx = 0.5f * K.ax, hy = 0.5f * K.ay;
+    Fx[0] = hx * G2[0].v.x; Fx[1] = hx * G2[1].v.x; Fx[2] = hx * G2[2].v.x; Fx[3] = hx * G2[3].v.x;
+    Fx[4] = hx * G2[4].v.x;
+    Fy[0] = hy * G2[0].v.y; Fy[1] = hy * G2[2].v.y; Fy[2] = hy * G2[1].v.y; Fy[3] = hy * G2[3].v.y;
+    Fy[4] = hy * G2[4].v.y;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) { Fx[5 + s] = hx * G2[5 + s].v.x; Fy[5 + s] = hy * G2[5 + s].v.y; }
 }
 
 template <typename T> __device__ __forceinline__ T min9(T a, T b, T c, T d, T e, T f, T g, T h, T i)
@@ -358,15 +389,18 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
             Wl.Mq = shup(W0.Mq, 1);
 #pragma unroll
             for (int s = 0; s < NS; ++s) Wl.k[s] = shup(W0.k[s], 1);
-            // (the halo rows need none of their faces but the top row's south face)
+            // (the halo rows need none of their faces but the top row's south face; FP32 evaluates
+            //  the x- and y-faces together as packed pairs)
             T Fw[NV], Fs[NV], Fb[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) Fw[v] = Fs[v] = Fb[v] = T(0);
-            if (wy > 0) face3<T, NS>(S, W0, 1, s1y, K.ay, K, eps1, xi_form, Fs);
-            if (wy > 0 && wy < TY3 - 1) {
-                face3<T, NS>(Wl, W0, 0, s1x, K.ax, K, eps1, xi_form, Fw);
-                face3<T, NS>(Wm, W0, 2, s1z, K.az, K, eps1, xi_form, Fb);
+            if constexpr (sizeof(T) == 4) {
+                if (wy > 0) faces3_xy<NS>(Wl, S, W0, s1x, s1y, K, eps1, xi_form, Fw, Fs);
+            } else {
+                if (wy > 0) face3<T, NS>(S, W0, 1, s1y, K.ay, K, eps1, xi_form, Fs);
+                if (wy > 0 && wy < TY3 - 1) face3<T, NS>(Wl, W0, 0, s1x, K.ax, K, eps1, xi_form, Fw);
             }
+            if (wy > 0 && wy < TY3 - 1) face3<T, NS>(Wm, W0, 2, s1z, K.az, K, eps1, xi_form, Fb);
 
             // the north neighbour's south flux
 #pragma unroll
