@@ -6,9 +6,11 @@
 // warp = row (one halo column and row on each side), and marches along z over a segment of
 // planes. Each thread keeps its cell's primitives for planes k-1, k, k+1 in registers (the
 // z-faces and their detector values), exchanges plane k with its x-neighbours by shuffles and
-// with its y-neighbours through shared memory (double-buffered by plane parity), and evaluates
-// the west x-face, the south y-face and the bottom z-face of its cell; a cell's east, north
-// and top fluxes come from the neighbouring lane, warp and the next plane.
+// with its y-neighbours through shared memory (double-buffered by plane parity, one block
+// barrier per plane: the row above's south flux of plane k is read after the barrier of
+// plane k + 1), and evaluates the west x-face, the south y-face and the bottom z-face of its
+// cell; a cell's east, north and top fluxes come from the neighbouring lane, warp and the
+// next plane.
 #pragma once
 
 #include "roeam_kernels.cuh"
@@ -361,6 +363,11 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
             at(b, NC + 1, wy, lane) = Pz;
             at(b, NC + 2, wy, lane) = Pzt;
             __syncthreads();
+            // the north neighbour's south flux of plane k - 1 (written after the previous barrier)
+            if (k > k0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] -= at(b ^ 1, NC + 3 + v, yn, lane);
+            }
             C3<T, NS> S;   // the cell below (row j - 1)
             S.r = at(b, 0, ys, lane); S.u = at(b, 1, ys, lane); S.v = at(b, 2, ys, lane); S.w = at(b, 3, ys, lane);
             S.p = at(b, 4, ys, lane); S.c2 = at(b, 5, ys, lane); S.H = at(b, 6, ys, lane); S.sr = at(b, 7, ys, lane);
@@ -402,10 +409,9 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
             }
             if (wy > 0 && wy < TY3 - 1) face3<T, NS>(Wm, W0, 2, s1z, K.az, K, eps1, xi_form, Fb);
 
-            // the north neighbour's south flux
+            // this plane's south flux, read by the row below after the next plane's barrier
 #pragma unroll
             for (int v = 0; v < NV; ++v) at(b, NC + 3 + v, wy, lane) = Fs[v];
-            __syncthreads();
 
             // finish plane k - 1: R = (acc - F_top) / V, then the stage combination
             if (k > k0 && out_cell) {
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 Un[v] = Un_next[v];
-                acc[v] = Fw[v] - shdn(Fw[v], 1) + Fs[v] - at(b, NC + 3 + v, yn, lane) + Fb[v];
+                acc[v] = Fw[v] - shdn(Fw[v], 1) + Fs[v] + Fb[v];
             }
 
             // advance the window
