@@ -48,7 +48,7 @@ typedef enum {
     ROEAM_E_STATE = 7         /* call not valid in the handle's current state */
 } roeam_status;
 
-enum { ROEAM_BC_PERIODIC = 0, ROEAM_BC_WALL = 1, ROEAM_BC_INFLOW = 2, ROEAM_BC_OUTFLOW = 3 };
+enum { ROEAM_BC_PERIODIC = 0, ROEAM_BC_WALL = 1, ROEAM_BC_INFLOW = 2, ROEAM_BC_OUTFLOW = 3, ROEAM_BC_EXCHANGE = 4 };
 enum { ROEAM_RECON_FIRST = 0, ROEAM_RECON_MINMOD = 1, ROEAM_RECON_VANLEER = 2 };
 enum { ROEAM_NORM_L2 = 0, ROEAM_NORM_LINF = 1 };
 
@@ -95,7 +95,9 @@ typedef struct {
  *   bc[4]      boundary type of the W (i = 0), E (i = ni-1), S (j = 0), N (j = nj-1) sides.
  *              PERIODIC must be set on both sides of a direction. WALL mirrors the
  *              adjacent state about the face normal; INFLOW imposes `inflow`;
- *              OUTFLOW copies the adjacent state (zero gradient).
+ *              OUTFLOW copies the adjacent state (zero gradient). EXCHANGE (S and N only)
+ *              takes the two ghost rows beyond the side from roeam_set_halo: the grid is a row
+ *              slab of a larger grid whose neighbouring slab lives elsewhere (another GPU).
  *   inflow     (rho, u, v, p) used by INFLOW sides.
  *   xv, yv     host float64 vertex coordinates, shape [nj+1][ni+1], or both NULL for a
  *              Cartesian grid with spacings dx, dy (> 0). For curvilinear grids dx, dy >= 0
@@ -150,6 +152,33 @@ roeam_status roeam_flux_residual(roeam_grid *g, int grid_idx, double *res_out);
  * dt_last (nullable, `count` doubles) receives each grid's dt of the last step (this
  * synchronises). */
 roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_last);
+
+/* Stage-by-stage stepping, for a grid split into row slabs over several GPUs (one handle per
+ * slab, S/N sides between slabs of type EXCHANGE). One SSP-RK3 step is three calls, stage =
+ * 0, 1, 2 in order, each advancing every grid of the handle with the same dt (> 0); between
+ * them the caller refreshes the ghost rows of EXCHANGE sides: before stage s, copy the
+ * neighbour's roeam_edge_rows(..., s, ...) into roeam_set_halo. A step begun this way must be
+ * finished before roeam_rk_step runs (ROEAM_E_STATE otherwise). The global time step is
+ * CFL / max over all slabs of roeam_max_rate. */
+roeam_status roeam_rk_stage(roeam_grid *g, int stage, double dt);
+
+/* Per-grid largest signal-speed rate sum_dir (|U| + max(c, c~/theta))|S_dir| / V of the current
+ * state (rate_out: `count` doubles); CFL / rate is the grid's time step. Synchronises and reports
+ * pending device errors. */
+roeam_status roeam_max_rate(roeam_grid *g, double *rate_out);
+
+/* Copies the two rows of grid grid_idx nearest side (2 = S: rows 0, 1; 3 = N: rows nj-2, nj-1)
+ * of the state that stage `stage` (0, 1, 2) reads (U^n, U1, U2) into dst, laid out
+ * [4 variables][2 rows, j increasing][ni] in the handle's precision (float or double). dst may
+ * be host or device memory; the copy is ordered on the handle's stream and, for host memory,
+ * complete on return. */
+roeam_status roeam_edge_rows(roeam_grid *g, int grid_idx, int side, int stage, void *dst);
+
+/* Sets the two ghost rows beyond the EXCHANGE side `side` (2 = S: j = -2, -1; 3 = N: j = nj,
+ * nj+1) of grid grid_idx from src, laid out like roeam_edge_rows' output (host or device
+ * memory; ordered on the handle's stream). The rows stay until set again; they start at zero,
+ * so they must be set before the first stage. */
+roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, const void *src);
 
 /* FP64 norm of the residual R(U) of grid `grid_idx` over its fluid cells, per variable:
  * kind ROEAM_NORM_L2 gives sqrt(mean R^2), ROEAM_NORM_LINF gives max |R|. Synchronises. */

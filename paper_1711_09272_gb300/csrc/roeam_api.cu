@@ -78,6 +78,9 @@ struct roeam_grid {
     void *U = nullptr, *A = nullptr, *B = nullptr;      // U^n (in place), stage buffers
     void *vdx = nullptr, *vdy = nullptr;
     uint8_t *solid = nullptr;
+    void *halo = nullptr;            // ghost rows of EXCHANGE sides (working precision)
+    long long total_halo = 0;
+    int stage_next = 0;              // next stage of a step run stage by stage (roeam_rk_stage)
     double *staging = nullptr;
     unsigned long long *rate = nullptr;                  // 2 x count slots (double bits)
     unsigned *status = nullptr;
@@ -208,6 +211,7 @@ StageArgs<T> base_args(roeam_grid *g)
     a.vdx = (const T *)g->vdx;
     a.vdy = (const T *)g->vdy;
     a.solid = g->solid;
+    a.halo = (const T *)g->halo;
     a.status = g->status;
     return a;
 }
@@ -462,7 +466,11 @@ roeam_status validate(int count, const roeam_grid_desc *d)
                 }
         }
         for (int s = 0; s < 4; ++s)
-            if (q.bc[s] < 0 || q.bc[s] > 3) return fail(ROEAM_E_ARG, "grid %d: bad boundary type on side %d", k, s);
+            if (q.bc[s] < 0 || q.bc[s] > 4) return fail(ROEAM_E_ARG, "grid %d: bad boundary type on side %d", k, s);
+        if (q.bc[0] == ROEAM_BC_EXCHANGE || q.bc[1] == ROEAM_BC_EXCHANGE)
+            return fail(ROEAM_E_ARG, "grid %d: EXCHANGE is for the S and N sides (row slabs)", k);
+        if (q.solid && (q.bc[2] == ROEAM_BC_EXCHANGE || q.bc[3] == ROEAM_BC_EXCHANGE))
+            return fail(ROEAM_E_ARG, "grid %d: solid cells cannot be combined with EXCHANGE sides", k);
         if ((q.bc[0] == ROEAM_BC_PERIODIC) != (q.bc[1] == ROEAM_BC_PERIODIC) ||
             (q.bc[2] == ROEAM_BC_PERIODIC) != (q.bc[3] == ROEAM_BC_PERIODIC))
             return fail(ROEAM_E_ARG, "grid %d: PERIODIC must be set on both sides of a direction", k);
@@ -474,6 +482,34 @@ roeam_status validate(int count, const roeam_grid_desc *d)
     }
     return ROEAM_OK;
 }
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+roeam_status do_stage(roeam_grid *g, int stage, double dt)
+{
+    const int par = (int)(g->step & 1);
+    unsigned long long *rd = g->rate + (size_t)par * g->count;
+    unsigned long long *wr = g->rate + (size_t)(1 - par) * g->count;
+    T *U = (T *)g->U, *A = (T *)g->A, *B = (T *)g->B;
+    StageArgs<T> a = base_args<T>(g);
+    a.mode = MODE_STAGE;
+    a.rate_rd = rd;
+    a.dt_fixed = dt;
+    a.dt_fixed_t = T(dt);
+    a.cfl_t = T(1);
+    if (stage == 0) { a.src = U; a.un = U; a.dst = A; a.alpha = T(0); a.beta = T(1); a.rate_zero = wr; }
+    else if (stage == 1) { a.src = A; a.un = U; a.dst = B; a.alpha = T(0.75); a.beta = T(0.25); }
+    else { a.src = B; a.un = U; a.dst = U; a.alpha = T(1.0 / 3.0); a.beta = T(2.0 / 3.0); a.rate_wr = wr; a.want_rate = 1; }
+    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, g->stream));
+    g->launches += 1;
+    return ROEAM_OK;
+}
+
+// The state buffer that stage `stage` reads: U^n, U1 or U2.
+void *stage_source(roeam_grid *g, int stage) { return stage == 0 ? g->U : (stage == 1 ? g->A : g->B); }
 
 }  // namespace
 
@@ -544,13 +580,19 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
             G.soff = -1;
         }
         G.nfluid = (double)nf;
+        if (q.bc[2] == ROEAM_BC_EXCHANGE || q.bc[3] == ROEAM_BC_EXCHANGE) {
+            G.hoff = g->total_halo;
+            g->total_halo += 16ll * G.pitch;   // 4 variables x 4 ghost rows
+        } else {
+            G.hoff = -1;
+        }
         G.poff = poff;
         poff += 4ll * q.ni * q.nj;
         g->max_cells = std::max(g->max_cells, q.ni * q.nj);
         for (int s = 0; s < 4; ++s) G.bc[s] = q.bc[s];
         bool walls = q.solid != nullptr;
         for (int s = 0; s < 4; ++s)
-            if (q.bc[s] == ROEAM_BC_WALL) walls = true;
+            if (q.bc[s] == ROEAM_BC_WALL || q.bc[s] == ROEAM_BC_EXCHANGE) walls = true;   // (ghost-row reads)
         const bool ablation = q.p.scheme != ROEAM_SCHEME_ROEAM || q.p.dup_mode != ROEAM_DUP_ROEAM || q.p.no_ufix ||
                               q.p.xi_roe;
         if (ablation) g->kind = KIND_ABLATION;
@@ -600,6 +642,10 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
         CREATE_TRY(cudaMalloc(&g->vdx, g->esize * (size_t)g->total_vert));
         CREATE_TRY(cudaMalloc(&g->vdy, g->esize * (size_t)g->total_vert));
     }
+    if (g->total_halo > 0) {
+        CREATE_TRY(cudaMalloc(&g->halo, g->esize * (size_t)g->total_halo));
+        CREATE_TRY(cudaMemset(g->halo, 0, g->esize * (size_t)g->total_halo));
+    }
     if (any_solid) {
         CREATE_TRY(cudaMalloc(&g->solid, (size_t)g->total_solid));
         std::vector<uint8_t> hs(g->total_solid, 0);
@@ -646,6 +692,7 @@ void roeam_destroy_grid(roeam_grid *g)
     cudaFree(g->vdx);
     cudaFree(g->vdy);
     cudaFree(g->solid);
+    cudaFree(g->halo);
     cudaFree(g->staging);
     cudaFree(g->rate);
     cudaFree(g->status);
@@ -696,6 +743,7 @@ roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nstep
     if (!std::isfinite(cfl) || !std::isfinite(dt_fixed)) return fail(ROEAM_E_ARG, "cfl and dt_fixed must be finite");
     for (int k = 0; k < g->count; ++k)
         if (!g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
+    if (g->stage_next != 0) return fail(ROEAM_E_STATE, "a step run by roeam_rk_stage is unfinished");
     CUDA_TRY(cudaSetDevice(g->device));
     const long long step0 = g->step;
     roeam_status st = g->precision == 32 ? rk_steps<float>(g, cfl, dt_fixed, nsteps)
@@ -839,6 +887,89 @@ long long roeam_cell_count(const roeam_grid *g, int grid_idx)
     if (!g || grid_idx < -1 || grid_idx >= g->count) return -1;
     if (grid_idx >= 0) return (long long)g->hg[grid_idx].ni * g->hg[grid_idx].nj;
     return g->total_packed / 4;
+}
+
+
+// ---- stage-by-stage stepping and ghost rows (row slabs of one grid on several GPUs)
+
+roeam_status roeam_max_rate(roeam_grid *g, double *rate_out)
+{
+    if (!g || !rate_out) return fail(ROEAM_E_ARG, "null argument");
+    CUDA_TRY(cudaSetDevice(g->device));
+    const int par = (int)(g->step & 1);
+    CUDA_TRY(cudaMemcpyAsync(g->h_rate, g->rate + (size_t)par * g->count, sizeof(unsigned long long) * g->count,
+                             cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (int k = 0; k < g->count; ++k) {
+        if (g->precision == 32) {
+            float f;
+            const uint32_t lo = (uint32_t)(g->h_rate[k] & 0xffffffffull);
+            std::memcpy(&f, &lo, sizeof(float));
+            rate_out[k] = (double)f;
+        } else {
+            std::memcpy(&rate_out[k], g->h_rate + k, sizeof(double));
+        }
+    }
+    return read_status(g);
+}
+
+
+roeam_status roeam_rk_stage(roeam_grid *g, int stage, double dt)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    if (stage < 0 || stage > 2) return fail(ROEAM_E_ARG, "stage must be 0, 1 or 2");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ROEAM_E_ARG, "dt must be finite and > 0");
+    if (stage != g->stage_next) return fail(ROEAM_E_STATE, "stage %d expected, %d given", g->stage_next, stage);
+    for (int k = 0; k < g->count; ++k)
+        if (!g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
+    CUDA_TRY(cudaSetDevice(g->device));
+    roeam_status st = g->precision == 32 ? do_stage<float>(g, stage, dt) : do_stage<double>(g, stage, dt);
+    if (st != ROEAM_OK) return st;
+    g->stage_next = (stage + 1) % 3;
+    if (stage == 2) g->step += 1;
+    return ROEAM_OK;
+}
+
+roeam_status roeam_edge_rows(roeam_grid *g, int grid_idx, int side, int stage, void *dst)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (grid_idx < 0) return fail(ROEAM_E_ARG, "edge rows need one grid (grid_idx >= 0)");
+    if (side != 2 && side != 3) return fail(ROEAM_E_ARG, "side must be 2 (S) or 3 (N)");
+    if (stage < 0 || stage > 2) return fail(ROEAM_E_ARG, "stage must be 0, 1 or 2");
+    if (!dst) return fail(ROEAM_E_ARG, "dst must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    const GridDev &G = g->hg[grid_idx];
+    const int r0 = side == 2 ? 0 : G.nj - 2;
+    const char *base = (const char *)stage_source(g, stage) + g->esize * (size_t)G.off;
+    for (int k = 0; k < 4; ++k)
+        CUDA_TRY(cudaMemcpy2DAsync((char *)dst + g->esize * (size_t)(2 * k * G.ni), g->esize * G.ni,
+                                   base + g->esize * (size_t)(k * G.plane + (long long)r0 * G.pitch),
+                                   g->esize * G.pitch, g->esize * G.ni, 2, cudaMemcpyDefault, g->stream));
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, dst) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+    }
+    return ROEAM_OK;
+}
+
+roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, const void *src)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (grid_idx < 0) return fail(ROEAM_E_ARG, "ghost rows need one grid (grid_idx >= 0)");
+    if (side != 2 && side != 3) return fail(ROEAM_E_ARG, "side must be 2 (S) or 3 (N)");
+    const GridDev &G = g->hg[grid_idx];
+    if (G.bc[side] != ROEAM_BC_EXCHANGE) return fail(ROEAM_E_ARG, "side %d of grid %d is not EXCHANGE", side, grid_idx);
+    if (!src) return fail(ROEAM_E_ARG, "src must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    char *base = (char *)g->halo + g->esize * (size_t)(G.hoff + (side == 2 ? 0 : 2) * (long long)G.pitch);
+    for (int k = 0; k < 4; ++k)
+        CUDA_TRY(cudaMemcpy2DAsync(base + g->esize * (size_t)(4ll * k * G.pitch), g->esize * G.pitch,
+                                   (const char *)src + g->esize * (size_t)(2 * k * G.ni), g->esize * G.ni,
+                                   g->esize * G.ni, 2, cudaMemcpyDefault, g->stream));
+    return ROEAM_OK;
 }
 
 }  // extern "C"

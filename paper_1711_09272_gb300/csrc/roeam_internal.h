@@ -8,7 +8,7 @@
 
 namespace roeam {
 
-constexpr int BC_PERIODIC = 0, BC_WALL = 1, BC_INFLOW = 2, BC_OUTFLOW = 3;
+constexpr int BC_PERIODIC = 0, BC_WALL = 1, BC_INFLOW = 2, BC_OUTFLOW = 3, BC_EXCHANGE = 4;
 
 // Status bits raised by kernels (read back by the host at synchronising calls).
 constexpr unsigned ST_NONPOSITIVE = 1u, ST_NONFINITE = 2u;
@@ -20,6 +20,8 @@ struct GridDev {
     long long voff;   // element offset of this grid's vertex displacement planes (-1: Cartesian)
     long long soff;   // byte offset of this grid's solid mask (-1: none)
     long long poff;   // element offset of this grid in the packed host layout [4][nj][ni]
+    long long hoff;   // element offset of this grid's ghost rows in the halo buffer (-1: none):
+                      // [4 variables][rows j = -2, -1, nj, nj + 1][pitch]
     int ni, nj, pitch, vpitch;
     int ntx, nty, tile_base, ntiles;
     int bc[4];        // W, E, S, N
@@ -58,6 +60,7 @@ struct StageArgs {
     T *dst;                 // stage output, or the residual in MODE_RESIDUAL
     const T *vdx, *vdy;     // vertex displacement planes (curvilinear grids)
     const uint8_t *solid;   // solid masks
+    const T *halo;          // ghost rows of EXCHANGE sides (slabs of a grid split across GPUs)
     T alpha, beta;          // dst = alpha * U^n + beta * (U^(k) + dt R(U^(k)))
     int mode;
     int want_rate;          // write each grid's max signal-speed rate of dst into rate_wr

@@ -26,6 +26,7 @@ EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_
            "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
            "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
            "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc",
+           "roeam_rk_stage", "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo",
            "roeam3_create_grid", "roeam3_destroy_grid", "roeam3_set_state", "roeam3_get_state",
            "roeam3_flux_residual", "roeam3_rk_step", "roeam3_conserved_totals", "roeam3_check",
            "roeam3_launch_count"]
@@ -90,6 +91,10 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_set_tile_config.argtypes = [vp, C.c_int]
     lib.roeam_autotune.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
     lib.roeam_flux_residual_noalloc.argtypes = [vp, C.c_int, vp]
+    lib.roeam_rk_stage.argtypes = [vp, C.c_int, C.c_double]
+    lib.roeam_max_rate.argtypes = [vp, dp]
+    lib.roeam_edge_rows.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
+    lib.roeam_set_halo.argtypes = [vp, C.c_int, C.c_int, vp]
     lib.roeam3_create_grid.argtypes = [C.c_int, C.POINTER(roeam3_grid_desc), C.c_int, vp, C.POINTER(vp)]
     lib.roeam3_destroy_grid.argtypes = [vp]
     lib.roeam3_destroy_grid.restype = None
@@ -103,7 +108,8 @@ def load_library(path: str = LIB_PATH):
     lib.roeam3_launch_count.restype = C.c_ulonglong
     for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
-                 "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam3_create_grid",
+                 "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam_rk_stage",
+                 "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam3_create_grid",
                  "roeam3_set_state", "roeam3_get_state", "roeam3_flux_residual", "roeam3_rk_step",
                  "roeam3_conserved_totals", "roeam3_check"):
         getattr(lib, name).restype = C.c_int
@@ -209,6 +215,24 @@ def roeam_autotune(h: int, cfl: float = 0.5, steps: int = 3):
     _check(load_library().roeam_autotune(C.c_void_p(h), cfl, steps, C.byref(best),
                                          ms.ctypes.data_as(C.POINTER(C.c_double))))
     return best.value, ms
+
+
+def roeam_rk_stage(h: int, stage: int, dt: float) -> None:
+    _check(load_library().roeam_rk_stage(C.c_void_p(h), stage, dt))
+
+
+def roeam_max_rate(h: int, count: int) -> np.ndarray:
+    out = np.zeros(count)
+    _check(load_library().roeam_max_rate(C.c_void_p(h), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def roeam_edge_rows(h: int, grid_idx: int, side: int, stage: int, dst) -> None:
+    _check(load_library().roeam_edge_rows(C.c_void_p(h), grid_idx, side, stage, C.c_void_p(_ptr(dst))))
+
+
+def roeam_set_halo(h: int, grid_idx: int, side: int, src) -> None:
+    _check(load_library().roeam_set_halo(C.c_void_p(h), grid_idx, side, C.c_void_p(_ptr(src))))
 
 
 # ----------------------------------------------------------------------------- convenience
@@ -320,6 +344,27 @@ class Batch:
 
     def autotune(self, cfl: float = 0.5, steps: int = 3):
         return roeam_autotune(self.handle, cfl, steps)
+
+    # stage-by-stage stepping of row slabs (EXCHANGE sides; see include/roeam.h)
+    def stage(self, stage: int, dt: float):
+        roeam_rk_stage(self.handle, stage, dt)
+
+    def max_rate(self) -> np.ndarray:
+        return roeam_max_rate(self.handle, len(self.specs))
+
+    def edge_rows(self, grid_idx: int, side: int, stage: int, out=None):
+        """The two rows nearest `side` (2 = S, 3 = N) of the state stage `stage` reads, as
+        (4, 2, ni) in the handle's precision; `out` may be a device tensor."""
+        s = self.specs[grid_idx]
+        if out is None:
+            out = np.empty((4, 2, s.ni), dtype=np.float32 if self.precision == 32 else np.float64)
+        roeam_edge_rows(self.handle, grid_idx, side, stage, out)
+        return out
+
+    def set_halo(self, grid_idx: int, side: int, rows):
+        if not hasattr(rows, "data_ptr"):
+            rows = np.ascontiguousarray(rows, dtype=np.float32 if self.precision == 32 else np.float64)
+        roeam_set_halo(self.handle, grid_idx, side, rows)
 
     @property
     def launches(self) -> int:
