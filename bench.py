@@ -274,6 +274,22 @@ def ablation_speed(P, torch, count=512, steps=50):
             "gcell_updates_per_s_per_stage": ncells * 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms}
 
 
+def small_configs(P, torch):
+    """The small paper-scale workloads, reported for latency (too small to load the HBM): the
+    64^2 isentropic vortex (FP64, 100 steps), the 256^2 Gresho vortex at M = 0.01 (MUSCL
+    minmod, FP32 and FP64, 2000 steps) and the 800 x 20 Quirk duct (FP32, CFL 0.25, 4000 steps):
+    device ms per step through graph replays."""
+    out = {}
+    spec, U = W.isentropic_vortex(64)
+    out["vortex_64_fp64"] = {"ms_per_step": time_single(P, torch, spec, U, 64, 100)[0], "steps": 100}
+    for prec in (32, 64):
+        spec, U = W.gresho(256, mach=0.01)
+        out[f"gresho_256_fp{prec}"] = {"ms_per_step": time_single(P, torch, spec, U, prec, 2000)[0], "steps": 2000}
+    spec, U = W.quirk(800, 20, eps_y=1e-6)
+    out["quirk_800x20_fp32"] = {"ms_per_step": time_single(P, torch, spec, U, 32, 4000, cfl=0.25)[0], "steps": 4000}
+    return out
+
+
 def _oracle_worker(job):
     """One host process of the all-cores CPU baseline: steps grids w, w + P, w + 2P, ... of the
     seeded batch with the oracle for `budget` seconds of wall time; returns the cell-stages."""
@@ -459,6 +475,7 @@ def run_ours(args):
             line["curvilinear"] = warped_step_speed(P, torch)
             line["three_d"] = three_d_speed(P, torch)
             line["ablation_roe"] = ablation_speed(P, torch)
+            line["small_configs"] = small_configs(P, torch)
         print(json.dumps(line), flush=True)
     b.close()
     if world > 1:
@@ -478,7 +495,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work-unit shape")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP32/FP64 and curvilinear side measurements")
-    ap.add_argument("--only", choices=["three_d", "ablation_roe", "curvilinear"],
+    ap.add_argument("--only", choices=["three_d", "ablation_roe", "curvilinear", "small_configs"],
                     help="run one side measurement alone and print its JSON (profiling runs)")
     ap.add_argument("--n3", type=int, default=256, help="cells per side of the 3D side measurement")
     args = ap.parse_args()
@@ -490,7 +507,8 @@ def main():
         P.load_library()
         fn = {"three_d": lambda: three_d_speed(P, torch, n=args.n3),
               "ablation_roe": lambda: ablation_speed(P, torch),
-              "curvilinear": lambda: warped_step_speed(P, torch)}[args.only]
+              "curvilinear": lambda: warped_step_speed(P, torch),
+              "small_configs": lambda: small_configs(P, torch)}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     if args.impl == "reference":

@@ -157,7 +157,7 @@ roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nstep
  * slab, S/N sides between slabs of type EXCHANGE). One SSP-RK3 step is three calls, stage =
  * 0, 1, 2 in order, each advancing every grid of the handle with the same dt (> 0); between
  * them the caller refreshes the ghost rows of EXCHANGE sides: before stage s, copy the
- * neighbour's roeam_edge_rows(..., s, ...) into roeam_set_halo. A step begun this way must be
+ * neighbour's roeam_edge_rows(..., s, ...) into roeam_set_halo(..., s, ...). A step begun this way must be
  * finished before roeam_rk_step runs (ROEAM_E_STATE otherwise). The global time step is
  * CFL / max over all slabs of roeam_max_rate. */
 roeam_status roeam_rk_stage(roeam_grid *g, int stage, double dt);
@@ -175,10 +175,11 @@ roeam_status roeam_max_rate(roeam_grid *g, double *rate_out);
 roeam_status roeam_edge_rows(roeam_grid *g, int grid_idx, int side, int stage, void *dst);
 
 /* Sets the two ghost rows beyond the EXCHANGE side `side` (2 = S: j = -2, -1; 3 = N: j = nj,
- * nj+1) of grid grid_idx from src, laid out like roeam_edge_rows' output (host or device
- * memory; ordered on the handle's stream). The rows stay until set again; they start at zero,
- * so they must be set before the first stage. */
-roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, const void *src);
+ * nj+1) of grid grid_idx, in the state that stage `stage` (0, 1, 2) reads, from src laid out
+ * like roeam_edge_rows' output (host or device memory; ordered on the handle's stream). A grid
+ * with an EXCHANGE side keeps these rows in its own state planes; they start at zero, so each
+ * must be set before the stage that reads it. */
+roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, const void *src);
 
 /* FP64 norm of the residual R(U) of grid `grid_idx` over its fluid cells, per variable:
  * kind ROEAM_NORM_L2 gives sqrt(mean R^2), ROEAM_NORM_LINF gives max |R|. Synchronises. */

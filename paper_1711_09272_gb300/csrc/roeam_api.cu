@@ -78,8 +78,6 @@ struct roeam_grid {
     void *U = nullptr, *A = nullptr, *B = nullptr;      // U^n (in place), stage buffers
     void *vdx = nullptr, *vdy = nullptr;
     uint8_t *solid = nullptr;
-    void *halo = nullptr;            // ghost rows of EXCHANGE sides (working precision)
-    long long total_halo = 0;
     int stage_next = 0;              // next stage of a step run stage by stage (roeam_rk_stage)
     double *staging = nullptr;
     unsigned long long *rate = nullptr;                  // 2 x count slots (double bits)
@@ -211,7 +209,6 @@ StageArgs<T> base_args(roeam_grid *g)
     a.vdx = (const T *)g->vdx;
     a.vdy = (const T *)g->vdy;
     a.solid = g->solid;
-    a.halo = (const T *)g->halo;
     a.status = g->status;
     return a;
 }
@@ -560,8 +557,10 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
         G.ni = q.ni;
         G.nj = q.nj;
         G.pitch = (int)round_up(q.ni, 32);
-        G.plane = (long long)q.nj * G.pitch;
-        G.off = off;
+        const bool exch = q.bc[2] == ROEAM_BC_EXCHANGE || q.bc[3] == ROEAM_BC_EXCHANGE;
+        // (a grid with an EXCHANGE side keeps two ghost rows below and above in its planes)
+        G.plane = (long long)(q.nj + (exch ? 4 : 0)) * G.pitch;
+        G.off = off + (exch ? 2ll * G.pitch : 0);
         off += 4 * G.plane;
         if (g->curv) {
             G.vpitch = (int)round_up(q.ni + 1, 32);
@@ -580,19 +579,13 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
             G.soff = -1;
         }
         G.nfluid = (double)nf;
-        if (q.bc[2] == ROEAM_BC_EXCHANGE || q.bc[3] == ROEAM_BC_EXCHANGE) {
-            G.hoff = g->total_halo;
-            g->total_halo += 16ll * G.pitch;   // 4 variables x 4 ghost rows
-        } else {
-            G.hoff = -1;
-        }
         G.poff = poff;
         poff += 4ll * q.ni * q.nj;
         g->max_cells = std::max(g->max_cells, q.ni * q.nj);
         for (int s = 0; s < 4; ++s) G.bc[s] = q.bc[s];
         bool walls = q.solid != nullptr;
         for (int s = 0; s < 4; ++s)
-            if (q.bc[s] == ROEAM_BC_WALL || q.bc[s] == ROEAM_BC_EXCHANGE) walls = true;   // (ghost-row reads)
+            if (q.bc[s] == ROEAM_BC_WALL) walls = true;
         const bool ablation = q.p.scheme != ROEAM_SCHEME_ROEAM || q.p.dup_mode != ROEAM_DUP_ROEAM || q.p.no_ufix ||
                               q.p.xi_roe;
         if (ablation) g->kind = KIND_ABLATION;
@@ -642,10 +635,6 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
         CREATE_TRY(cudaMalloc(&g->vdx, g->esize * (size_t)g->total_vert));
         CREATE_TRY(cudaMalloc(&g->vdy, g->esize * (size_t)g->total_vert));
     }
-    if (g->total_halo > 0) {
-        CREATE_TRY(cudaMalloc(&g->halo, g->esize * (size_t)g->total_halo));
-        CREATE_TRY(cudaMemset(g->halo, 0, g->esize * (size_t)g->total_halo));
-    }
     if (any_solid) {
         CREATE_TRY(cudaMalloc(&g->solid, (size_t)g->total_solid));
         std::vector<uint8_t> hs(g->total_solid, 0);
@@ -692,7 +681,6 @@ void roeam_destroy_grid(roeam_grid *g)
     cudaFree(g->vdx);
     cudaFree(g->vdy);
     cudaFree(g->solid);
-    cudaFree(g->halo);
     cudaFree(g->staging);
     cudaFree(g->rate);
     cudaFree(g->status);
@@ -954,7 +942,7 @@ roeam_status roeam_edge_rows(roeam_grid *g, int grid_idx, int side, int stage, v
     return ROEAM_OK;
 }
 
-roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, const void *src)
+roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, const void *src)
 {
     roeam_status st = check_idx(g, grid_idx);
     if (st != ROEAM_OK) return st;
@@ -962,11 +950,13 @@ roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, const void *s
     if (side != 2 && side != 3) return fail(ROEAM_E_ARG, "side must be 2 (S) or 3 (N)");
     const GridDev &G = g->hg[grid_idx];
     if (G.bc[side] != ROEAM_BC_EXCHANGE) return fail(ROEAM_E_ARG, "side %d of grid %d is not EXCHANGE", side, grid_idx);
+    if (stage < 0 || stage > 2) return fail(ROEAM_E_ARG, "stage must be 0, 1 or 2");
     if (!src) return fail(ROEAM_E_ARG, "src must be non-null");
     CUDA_TRY(cudaSetDevice(g->device));
-    char *base = (char *)g->halo + g->esize * (size_t)(G.hoff + (side == 2 ? 0 : 2) * (long long)G.pitch);
+    const long long r0 = side == 2 ? -2 : G.nj;
+    char *base = (char *)stage_source(g, stage) + g->esize * (size_t)(G.off + r0 * G.pitch);
     for (int k = 0; k < 4; ++k)
-        CUDA_TRY(cudaMemcpy2DAsync(base + g->esize * (size_t)(4ll * k * G.pitch), g->esize * G.pitch,
+        CUDA_TRY(cudaMemcpy2DAsync(base + g->esize * (size_t)(k * G.plane), g->esize * G.pitch,
                                    (const char *)src + g->esize * (size_t)(2 * k * G.ni), g->esize * G.ni,
                                    g->esize * G.ni, 2, cudaMemcpyDefault, g->stream));
     return ROEAM_OK;

@@ -15,13 +15,12 @@ constexpr unsigned ST_NONPOSITIVE = 1u, ST_NONFINITE = 2u;
 
 // Per-grid descriptor, resident in device memory, read-only in kernels.
 struct GridDev {
-    long long off;    // element offset of this grid's variable-0 plane in the state buffers
-    long long plane;  // elements per variable plane (nj * pitch)
+    long long off;    // element offset of this grid's row 0 of variable 0 in the state buffers
+    long long plane;  // elements per variable plane (nj * pitch; (nj + 4) * pitch with an
+                      // EXCHANGE side, whose planes also hold the ghost rows j = -2, -1, nj, nj+1)
     long long voff;   // element offset of this grid's vertex displacement planes (-1: Cartesian)
     long long soff;   // byte offset of this grid's solid mask (-1: none)
     long long poff;   // element offset of this grid in the packed host layout [4][nj][ni]
-    long long hoff;   // element offset of this grid's ghost rows in the halo buffer (-1: none):
-                      // [4 variables][rows j = -2, -1, nj, nj + 1][pitch]
     int ni, nj, pitch, vpitch;
     int ntx, nty, tile_base, ntiles;
     int bc[4];        // W, E, S, N
@@ -60,7 +59,6 @@ struct StageArgs {
     T *dst;                 // stage output, or the residual in MODE_RESIDUAL
     const T *vdx, *vdy;     // vertex displacement planes (curvilinear grids)
     const uint8_t *solid;   // solid masks
-    const T *halo;          // ghost rows of EXCHANGE sides (slabs of a grid split across GPUs)
     T alpha, beta;          // dst = alpha * U^n + beta * (U^(k) + dt R(U^(k)))
     int mode;
     int want_rate;          // write each grid's max signal-speed rate of dst into rate_wr

@@ -364,8 +364,9 @@ template <> __device__ __forceinline__ double rate_value<double>(unsigned long l
 // Boundary resolution of one index direction: a cell index outside [0, n) maps to the
 // source index of its ghost value and a kind: 0 interior/periodic/outflow (a plain copy of
 // the source cell), 1 WALL (the source cell mirrored about the boundary face), 2 INFLOW (the
-// prescribed state), 3 EXCHANGE (row 0..3 of the grid's ghost rows j = -2, -1, n, n + 1, set by
-// the caller from the neighbouring slab). Indices beyond the two ghost layers (ragged strips) are clamped into the
+// prescribed state), 3 EXCHANGE (the ghost row itself, j = -2, -1, n or n + 1: a grid with an
+// EXCHANGE side stores those rows in its state planes, set by the caller from the
+// neighbouring slab). Indices beyond the two ghost layers (ragged strips) are clamped into the
 // grid; their values are never used.
 __device__ __forceinline__ int resolve_index(int x, int n, int bc_lo, int bc_hi, int &kind)
 {
@@ -374,7 +375,7 @@ __device__ __forceinline__ int resolve_index(int x, int n, int bc_lo, int bc_hi,
     const int bc = x < 0 ? bc_lo : bc_hi;
     int s;
     if (bc == BC_INFLOW) { kind = 2; s = 0; }
-    else if (bc == BC_EXCHANGE) { kind = 3; return clampi(x < 0 ? x + 2 : x - n + 2, 0, 3); }   // halo row
+    else if (bc == BC_EXCHANGE) { kind = 3; return clampi(x, -2, n + 1); }   // a ghost row kept in the planes
     else if (bc == BC_PERIODIC) s = ((x % n) + n) % n;
     else if (bc == BC_OUTFLOW) s = x < 0 ? 0 : n - 1;
     else { kind = 1; s = x < 0 ? -1 - x : 2 * n - 1 - x; }
@@ -576,7 +577,6 @@ template <typename T> struct GridRegs {
     T *dst;
     const T *vdx, *vdy;         // vertex displacement planes of this grid (curvilinear)
     const uint8_t *solid;       // solid mask of this grid, or null
-    const T *halo;              // ghost rows of EXCHANGE sides, or null
     int ni, nj, pitch, plane, vpitch;
     int bcW, bcE, bcS, bcN;
 };
@@ -593,20 +593,11 @@ template <typename T> struct Pending {
     int jsrc, ky;
 };
 
-// (ghost rows of EXCHANGE sides are read only by the kernels built for walls, which every
-//  batch with such a side runs)
-template <typename T, bool HALO>
+template <typename T>
 __device__ __forceinline__ void issue_cell(const GridRegs<T> &R, int isrc, int kx, int j, Pending<T> &q)
 {
     q.jsrc = resolve_index(j, R.nj, R.bcS, R.bcN, q.ky);
-    if (HALO && q.ky == 3 && kx != 2) {
-        const int x = q.jsrc * R.pitch + isrc;
-        const int hp = 4 * R.pitch;
-        q.raw[0] = __ldg(R.halo + x);
-        q.raw[1] = __ldg(R.halo + x + hp);
-        q.raw[2] = __ldg(R.halo + x + 2 * hp);
-        q.raw[3] = __ldg(R.halo + x + 3 * hp);
-    } else if (kx != 2 && q.ky != 2) {
+    if (kx != 2 && q.ky != 2) {
         const int x = q.jsrc * R.pitch + isrc;
         q.raw[0] = __ldg(R.src + x);
         q.raw[1] = __ldg(R.src + x + R.plane);
@@ -628,7 +619,8 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
         c.r = q.raw[0]; c.u = q.raw[1] * ri; c.v = q.raw[2] * ri;
         c.p = K.gm1 * (q.raw[3] - T(0.5) * q.raw[0] * (c.u * c.u + c.v * c.v));
         if constexpr (WALLS) {
-            if (R.solid && ky != 3 && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1;
+            // (grids with solid cells have no EXCHANGE side, so jsrc is a grid row here)
+            if (R.solid && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1;
         }
     }
     if constexpr (WALLS) {
@@ -708,7 +700,6 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         if constexpr (CURV) { R.vdx = a.vdx + G.voff; R.vdy = a.vdy + G.voff; R.vpitch = G.vpitch; }
         else { R.vdx = R.vdy = nullptr; R.vpitch = 0; }
         R.solid = (WALLS && G.soff >= 0) ? a.solid + G.soff : nullptr;
-        R.halo = (WALLS && G.hoff >= 0) ? a.halo + G.hoff : nullptr;
         const int ni = R.ni, nj = R.nj;
         const bool use_s1 = G.use_s1 != 0;
         const int eps1 = G.eps1, xi_form = G.xi_form;
@@ -753,13 +744,13 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         };
         for (int w = 0; w < NW; ++w) {
             const int jr = j0 - H + w;
-            issue_cell<T, WALLS>(R, isrc, kx, jr, pend);
+            issue_cell(R, isrc, kx, jr, pend);
             finish_cell<T, MUSCL, CURV, WALLS>(R, K, i, isrc, kx, jr, pend, Wn[w]);
             Px[w] = px_of(Wn[w]);
             if (w > 0) Py[w - 1] = py_of(Wn[w - 1], Wn[w]);
         }
         for (int v = 0; v < NV; ++v) vload(j0 - 1 + v, vX[v], vY[v]);
-        issue_cell<T, WALLS>(R, isrc, kx, j0 + 2, pend);
+        issue_cell(R, isrc, kx, j0 + 2, pend);
         T Un[4] = {T(0), T(0), T(0), T(0)};
         T acc[4] = {T(0), T(0), T(0), T(0)};
         T my_rate = T(0);
@@ -924,7 +915,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             finish_cell<T, MUSCL, CURV, WALLS>(R, K, i, isrc, kx, j + 2, pend, Wn[NW - 1]);
             Px[NW - 1] = px_of(Wn[NW - 1]);
             Py[NW - 2] = py_of(Wn[NW - 2], Wn[NW - 1]);
-            issue_cell<T, WALLS>(R, isrc, kx, j + 3, pend);
+            issue_cell(R, isrc, kx, j + 3, pend);
             if constexpr (CURV) {
                 for (int v = 0; v < NV - 1; ++v) { vX[v] = vX[v + 1]; vY[v] = vY[v + 1]; }
                 vload(j + 3, vX[NV - 1], vY[NV - 1]);

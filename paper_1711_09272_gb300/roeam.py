@@ -94,7 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_rk_stage.argtypes = [vp, C.c_int, C.c_double]
     lib.roeam_max_rate.argtypes = [vp, dp]
     lib.roeam_edge_rows.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
-    lib.roeam_set_halo.argtypes = [vp, C.c_int, C.c_int, vp]
+    lib.roeam_set_halo.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
     lib.roeam3_create_grid.argtypes = [C.c_int, C.POINTER(roeam3_grid_desc), C.c_int, vp, C.POINTER(vp)]
     lib.roeam3_destroy_grid.argtypes = [vp]
     lib.roeam3_destroy_grid.restype = None
@@ -231,8 +231,8 @@ def roeam_edge_rows(h: int, grid_idx: int, side: int, stage: int, dst) -> None:
     _check(load_library().roeam_edge_rows(C.c_void_p(h), grid_idx, side, stage, C.c_void_p(_ptr(dst))))
 
 
-def roeam_set_halo(h: int, grid_idx: int, side: int, src) -> None:
-    _check(load_library().roeam_set_halo(C.c_void_p(h), grid_idx, side, C.c_void_p(_ptr(src))))
+def roeam_set_halo(h: int, grid_idx: int, side: int, stage: int, src) -> None:
+    _check(load_library().roeam_set_halo(C.c_void_p(h), grid_idx, side, stage, C.c_void_p(_ptr(src))))
 
 
 # ----------------------------------------------------------------------------- convenience
@@ -361,10 +361,11 @@ class Batch:
         roeam_edge_rows(self.handle, grid_idx, side, stage, out)
         return out
 
-    def set_halo(self, grid_idx: int, side: int, rows):
+    def set_halo(self, grid_idx: int, side: int, stage: int, rows):
+        """Ghost rows beyond EXCHANGE side `side` of the state stage `stage` reads."""
         if not hasattr(rows, "data_ptr"):
             rows = np.ascontiguousarray(rows, dtype=np.float32 if self.precision == 32 else np.float64)
-        roeam_set_halo(self.handle, grid_idx, side, rows)
+        roeam_set_halo(self.handle, grid_idx, side, stage, rows)
 
     @property
     def launches(self) -> int:

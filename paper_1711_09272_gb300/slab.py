@@ -155,7 +155,7 @@ class SlabStepper:
             return
         inbox = self.ex.swap(outgoing, wanted)
         for (r, side), rows in inbox.items():
-            self.handles[r].set_halo(0, side, rows)
+            self.handles[r].set_halo(0, side, stage, rows)
 
     def dt(self, cfl: float) -> float:
         local = max(float(self.handles[r].max_rate()[0]) for r in self.mine)

@@ -38,7 +38,7 @@ class OracleSlab:
         S = self._source(stage)
         return (S[:, :2] if side == 2 else S[:, -2:]).copy()
 
-    def set_halo(self, idx, side, rows):
+    def set_halo(self, idx, side, stage, rows):
         self.halo[side] = np.array(rows, dtype=np.float64)
 
     def _residual(self, S):

@@ -43,7 +43,7 @@ def test_slabs_reproduce_the_whole_grid(case, prec):
     every cell sees the same neighbour values and the same dt. The results agree to a few
     units in the last place (not bit for bit: a row's position within its work unit decides
     which copy of the two-rows-per-trip loop body evaluates it, and the copies may fuse
-    multiply-adds differently; a slab also runs the kernel family built for walls)."""
+    multiply-adds differently)."""
     spec = CASES[case]()
     U = W.random_smooth_state(W.GridSpec(ni=spec.ni, nj=spec.nj, dx=spec.dx, dy=spec.dy, params=spec.params),
                               seed=9, mach=0.6, amp=0.3)
@@ -94,17 +94,17 @@ def test_exchange_api_errors():
     with P().Batch([spec], precision=64) as b:
         b.set_state(U, 0)
         with pytest.raises(P().RoeamError):
-            b.set_halo(0, 2, np.ones((4, 2, 32)))          # S is a wall
-        b.set_halo(0, 3, b.edge_rows(0, 3, 0))
+            b.set_halo(0, 2, 0, np.ones((4, 2, 32)))       # S is a wall
+        b.set_halo(0, 3, 0, b.edge_rows(0, 3, 0))
         with pytest.raises(P().RoeamError):
             b.stage(1, 1e-3)                                # stage 0 first
         b.stage(0, 1e-3)
         with pytest.raises(P().RoeamError) as e:
             b.step(0.5)
         assert e.value.status == 7
-        b.set_halo(0, 3, b.edge_rows(0, 3, 1))
+        b.set_halo(0, 3, 1, b.edge_rows(0, 3, 1))
         b.stage(1, 1e-3)
-        b.set_halo(0, 3, b.edge_rows(0, 3, 2))
+        b.set_halo(0, 3, 2, b.edge_rows(0, 3, 2))
         b.stage(2, 1e-3)
         b.step(0.5)                                         # a whole step works again
         assert np.all(np.isfinite(b.get_state(0)))
