@@ -146,7 +146,7 @@ __device__ __forceinline__ void roeam_flux3(const FS3<V, NS> &L, const FS3<V, NS
     const V dp = R.p - L.p;
 
     const V br = sel(lt(aU, ch), splat<V>(2), sel(eq(aU, ch), one, zero));
-    const V Up = sel(gt(du, zero), vmax(vfma(splat<V>(S(-0.25)) * fMb * br, du, aU), zero), aU);
+    const V Up = vmax(vfma(splat<V>(S(-0.25)) * fMb * br, vmax(du, zero), aU), zero);   // du <= 0 leaves |U|
 
     const V xfac = xi_form ? one : one - fMb8;
     V xi = vmax(vfma(xfac * half, du, vabs(half * (L.un + R.un))), zero);

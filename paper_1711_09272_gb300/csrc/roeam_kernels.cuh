@@ -231,7 +231,8 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
 
     // |U|': the bracket sgn(U + c) - sgn(U - c) is 2 for |U| < c, 1 for |U| = c, 0 above.
     const V br = sel(lt(aU, ch), splat<V>(2), sel(eq(aU, ch), one, zero));
-    V Up = sel(gt(du, zero), vmax(vfma(splat<V>(S(-0.25)) * fMb * br, du, aU), zero), aU);
+    // (du <= 0 leaves |U|: the correction is applied to max(du, 0))
+    V Up = vmax(vfma(splat<V>(S(-0.25)) * fMb * br, vmax(du, zero), aU), zero);
     if constexpr (ABL) {
         if (!var.ufix) Up = aU;
     }
