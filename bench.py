@@ -495,7 +495,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work-unit shape")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP32/FP64 and curvilinear side measurements")
-    ap.add_argument("--only", choices=["three_d", "ablation_roe", "curvilinear", "small_configs"],
+    ap.add_argument("--only", choices=["three_d", "ablation_roe", "curvilinear", "small_configs",
+                                       "precision_comparison"],
                     help="run one side measurement alone and print its JSON (profiling runs)")
     ap.add_argument("--n3", type=int, default=256, help="cells per side of the 3D side measurement")
     args = ap.parse_args()
@@ -508,7 +509,8 @@ def main():
         fn = {"three_d": lambda: three_d_speed(P, torch, n=args.n3),
               "ablation_roe": lambda: ablation_speed(P, torch),
               "curvilinear": lambda: warped_step_speed(P, torch),
-              "small_configs": lambda: small_configs(P, torch)}[args.only]
+              "small_configs": lambda: small_configs(P, torch),
+              "precision_comparison": lambda: precision_comparison(P, torch)}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     if args.impl == "reference":

@@ -153,6 +153,12 @@ roeam_status roeam_flux_residual(roeam_grid *g, int grid_idx, double *res_out);
  * synchronises). */
 roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_last);
 
+/* Test hook (the paper has no counterpart): evaluates, on CUDA device `device`, the
+ * reciprocal, reciprocal square root and square root that the kernels use, for n (1..2^24)
+ * host values x > 0. out (6 n doubles) receives per value: 1/x, 1/sqrt(x), sqrt(x) in FP64,
+ * then the same three in FP32 of (float)x. Used to check them against the IEEE operations. */
+roeam_status roeam_math_check(int device, int n, const double *x, double *out);
+
 /* Stage-by-stage stepping, for a grid split into row slabs over several GPUs (one handle per
  * slab, S/N sides between slabs of type EXCHANGE). One SSP-RK3 step is three calls, stage =
  * 0, 1, 2 in order, each advancing every grid of the handle with the same dt (> 0); between

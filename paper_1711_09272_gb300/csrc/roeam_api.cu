@@ -962,6 +962,22 @@ roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, co
     return ROEAM_OK;
 }
 
+roeam_status roeam_math_check(int device, int n, const double *x, double *out)
+{
+    if (n < 1 || n > (1 << 24) || !x || !out) return fail(ROEAM_E_ARG, "need 1 <= n <= 2^24 and non-null x, out");
+    CUDA_TRY(cudaSetDevice(device));
+    double *dx = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&dx, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double) * 6 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_math_check(n, dx, dout, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(double) * 6 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(ROEAM_E_CUDA, "math check: %s", cudaGetErrorString(e));
+    return ROEAM_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------

@@ -131,6 +131,9 @@ struct AblationLaunchers {
     static int stage_occupancy(int muscl, int curv);
 };
 
+// The kernels' reciprocal, rsqrt and sqrt on n device values (n rows of 6 doubles; test hook).
+cudaError_t launch_math_check(int n, const double *x, double *out, cudaStream_t s);
+
 // Sets the thread's roeam_last_error() message and returns `status` (host).
 int record_error(int status, const char *msg);
 

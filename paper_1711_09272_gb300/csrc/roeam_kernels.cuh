@@ -69,8 +69,12 @@ template <typename T> __device__ __forceinline__ T sel(bool m, T a, T b) { retur
 __device__ __forceinline__ V2 sel(B2 m, V2 a, V2 b) { return mk2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y); }
 
 // Reciprocal, reciprocal square root and square root (of a non-negative value). FP32 uses
-// the single-instruction hardware approximations (PTX rcp/rsqrt/sqrt .approx); FP64 the
-// correctly rounded operations.
+// the single-instruction hardware approximations (PTX rcp/rsqrt/sqrt .approx). FP64 starts
+// from the hardware approximations (PTX rcp.approx.ftz.f64, rsqrt.approx.ftz.f64) and refines
+// them by two Newton-Raphson steps, each of which squares the relative error (y <- y + y e
+// with e = 1 - x y for 1/x, y <- y + y e / 2 with e = 1 - x y^2 for 1/sqrt(x)): within two
+// ulp of the correctly rounded results for the positive normal arguments the scheme produces
+// (roeam_math_check compares them with the IEEE operations), at a fraction of their cost.
 __device__ __forceinline__ float rcp(float x)
 {
     float r;
@@ -89,9 +93,25 @@ __device__ __forceinline__ float sqrt0(float x)
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ double sqrt0(double x) { return sqrt(x); }
+__device__ __forceinline__ double rcp(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+__device__ __forceinline__ double rsq(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    e = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+__device__ __forceinline__ double sqrt0(double x) { return x > 0.0 ? x * rsq(x) : 0.0; }
 __device__ __forceinline__ V2 rcp(V2 x) { return mk2(rcp(x.v.x), rcp(x.v.y)); }
 __device__ __forceinline__ V2 rsq(V2 x) { return mk2(rsq(x.v.x), rsq(x.v.y)); }
 __device__ __forceinline__ V2 sqrt0(V2 x) { return mk2(sqrt0(x.v.x), sqrt0(x.v.y)); }
@@ -803,22 +823,22 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             if constexpr (CURV) {
                 // x-face: vertices (i, j), (i, j+1); y-face: vertices (i, j), (i+1, j)
                 T sx = K.dy + (vY[2] - vY[1]), sy = -(vX[2] - vX[1]);
-                fx.len = sqrt(sx * sx + sy * sy);
-                T li = T(1) / fx.len;
+                fx.len = sqrt0(sx * sx + sy * sy);
+                T li = rcp(fx.len);
                 fx.nx = sx * li; fx.ny = sy * li;
                 const T xr = shdn(vX[1], 1), yr = shdn(vY[1], 1);
                 sx = -(yr - vY[1]); sy = K.dx + (xr - vX[1]);
-                fy.len = sqrt(sx * sx + sy * sy);
-                li = T(1) / fy.len;
+                fy.len = sqrt0(sx * sx + sy * sy);
+                li = rcp(fy.len);
                 fy.nx = sx * li; fy.ny = sy * li;
                 if constexpr (MUSCL) {
                     // normals of the faces Am|A and B|Bp of both faces (mirrors at solid cells)
                     fx.nAmx = shup(fx.nx, 1); fx.nAmy = shup(fx.ny, 1);
                     fx.nBpx = shdn(fx.nx, 1); fx.nBpy = shdn(fx.ny, 1);
                     const T x0 = shdn(vX[0], 1), y0 = shdn(vY[0], 1), x3 = shdn(vX[3], 1), y3 = shdn(vY[3], 1);
-                    T tx = -(y0 - vY[0]), ty = K.dx + (x0 - vX[0]), l = T(1) / sqrt(tx * tx + ty * ty);
+                    T tx = -(y0 - vY[0]), ty = K.dx + (x0 - vX[0]), l = rsq(tx * tx + ty * ty);
                     fy.nAmx = tx * l; fy.nAmy = ty * l;
-                    tx = -(y3 - vY[3]); ty = K.dx + (x3 - vX[3]); l = T(1) / sqrt(tx * tx + ty * ty);
+                    tx = -(y3 - vY[3]); ty = K.dx + (x3 - vX[3]); l = rsq(tx * tx + ty * ty);
                     fy.nBpx = tx * l; fy.nBpy = ty * l;
                 } else {
                     fx.nAmx = fx.nBpx = fx.nx; fx.nAmy = fx.nBpy = fx.ny;
@@ -874,7 +894,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 }
                 if (out_lane) {
                     const bool solid = WALLS && (Wn[H - 1].fl & 1);
-                    const T Vi = CURV ? T(1) / cg.V : K.Vi;
+                    const T Vi = CURV ? rcp(cg.V) : K.Vi;
                     T Rs[4];
                     for (int k = 0; k < 4; ++k) Rs[k] = solid ? T(0) : (acc[k] - Fs[k]) * Vi;
                     const int x = (j - 1) * R.pitch + i;

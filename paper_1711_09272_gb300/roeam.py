@@ -26,7 +26,7 @@ EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_
            "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
            "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
            "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc",
-           "roeam_rk_stage", "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo",
+           "roeam_rk_stage", "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check",
            "roeam3_create_grid", "roeam3_destroy_grid", "roeam3_set_state", "roeam3_get_state",
            "roeam3_flux_residual", "roeam3_rk_step", "roeam3_conserved_totals", "roeam3_check",
            "roeam3_launch_count"]
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_autotune.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
     lib.roeam_flux_residual_noalloc.argtypes = [vp, C.c_int, vp]
     lib.roeam_rk_stage.argtypes = [vp, C.c_int, C.c_double]
+    lib.roeam_math_check.argtypes = [C.c_int, C.c_int, dp, dp]
     lib.roeam_max_rate.argtypes = [vp, dp]
     lib.roeam_edge_rows.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
     lib.roeam_set_halo.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
@@ -109,7 +110,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
                  "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam_rk_stage",
-                 "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam3_create_grid",
+                 "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check", "roeam3_create_grid",
                  "roeam3_set_state", "roeam3_get_state", "roeam3_flux_residual", "roeam3_rk_step",
                  "roeam3_conserved_totals", "roeam3_check"):
         getattr(lib, name).restype = C.c_int
@@ -215,6 +216,15 @@ def roeam_autotune(h: int, cfl: float = 0.5, steps: int = 3):
     _check(load_library().roeam_autotune(C.c_void_p(h), cfl, steps, C.byref(best),
                                          ms.ctypes.data_as(C.POINTER(C.c_double))))
     return best.value, ms
+
+
+def roeam_math_check(x, device: int = 0) -> np.ndarray:
+    """(n, 6): the kernels' 1/x, 1/sqrt(x), sqrt(x) in FP64 and in FP32 (test hook)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((x.size, 6))
+    _check(load_library().roeam_math_check(device, x.size, x.ctypes.data_as(C.POINTER(C.c_double)),
+                                           out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
 
 
 def roeam_rk_stage(h: int, stage: int, dt: float) -> None:
