@@ -187,6 +187,16 @@ roeam_status roeam_edge_rows(roeam_grid *g, int grid_idx, int side, int stage, v
  * must be set before the stage that reads it. */
 roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, const void *src);
 
+/* The host-resident form of a step: loads every grid from cons_in (host float64, the layout of
+ * roeam_set_state with grid_idx = -1), advances nsteps SSP-RK3 steps as roeam_rk_step does, and
+ * writes the result to cons_out (same layout; it may equal cons_in), overlapping the copies
+ * with the computation: the grids go through in chunks of about an eighth of the cells, on two
+ * internal streams, each chunk copied in, stepped and copied out while its neighbours move.
+ * Page-locked host arrays make the copies asynchronous. The device state afterwards equals
+ * cons_out. dt_last as in roeam_rk_step. Synchronises; reports device errors. */
+roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const double *cons_in,
+                             double *cons_out, double *dt_last);
+
 /* FP64 norm of the residual R(U) of grid `grid_idx` over its fluid cells, per variable:
  * kind ROEAM_NORM_L2 gives sqrt(mean R^2), ROEAM_NORM_LINF gives max |R|. Synchronises. */
 roeam_status roeam_residual_norm(roeam_grid *g, int grid_idx, int kind, double out[4]);

@@ -59,6 +59,8 @@ struct roeam_grid {
     int device = 0;
     cudaStream_t stream = nullptr;       // user stream (work is ordered on it)
     cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
+    cudaStream_t pipe[2] = {nullptr, nullptr};   // roeam_step_host: chunks alternate between them
+    cudaEvent_t pipe_ev[3] = {nullptr, nullptr, nullptr};
     int precision = 32, muscl = 0, curv = 0, kind = KIND_PLAIN, count = 0;   // kind: StageKind
     size_t esize = 4;
     int tile_cfg = 0;
@@ -510,6 +512,53 @@ void *stage_source(roeam_grid *g, int stage) { return stage == 0 ? g->U : (stage
 
 }  // namespace
 
+namespace {
+
+// One chunk of roeam_step_host: grids [lo, hi) from the packed host input to the packed host
+// output through nsteps steps, all on stream s (steps use the per-grid unit table).
+template <typename T>
+roeam_status pipe_chunk(roeam_grid *g, int lo, int hi, int nsteps, double cfl, double dt_fixed, const double *in,
+                        double *out, cudaStream_t s)
+{
+    const long long p0 = g->hg[lo].poff;
+    const long long p1 = hi < g->count ? g->hg[hi].poff : g->total_packed;
+    CUDA_TRY(cudaMemcpyAsync(g->staging + p0, in + p0, sizeof(double) * (p1 - p0), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, g->staging, (T *)g->U, s));
+    unsigned long long *slot0 = g->rate + (size_t)(g->step & 1) * g->count;
+    CUDA_TRY(cudaMemsetAsync(slot0 + lo, 0, sizeof(unsigned long long) * (hi - lo), s));
+    CUDA_TRY(Launchers<T>::rate(g->d_grids, (const GridCoef<T> *)g->d_coef, lo, hi, (const T *)g->U,
+                                (const T *)g->vdx, (const T *)g->vdy, g->solid, slot0, g->curv, s));
+    T *U = (T *)g->U, *A = (T *)g->A, *B = (T *)g->B;
+    StageArgs<T> a = base_args<T>(g);
+    a.units = g->d_units_grid;
+    a.tile_lo = g->h_tile_base[lo];
+    a.tile_hi = g->h_tile_base[hi];
+    a.mode = MODE_STAGE;
+    a.cfl = cfl;
+    a.dt_fixed = dt_fixed;
+    a.cfl_t = T(cfl);
+    a.dt_fixed_t = T(dt_fixed);
+    for (long long st = g->step; st < g->step + nsteps; ++st) {
+        const int par = (int)(st & 1);
+        a.rate_rd = g->rate + (size_t)par * g->count;
+        unsigned long long *wr = g->rate + (size_t)(1 - par) * g->count;
+        CUDA_TRY(cudaMemsetAsync(wr + lo, 0, sizeof(unsigned long long) * (hi - lo), s));
+        a.rate_zero = nullptr;
+        a.src = U; a.un = U; a.dst = A; a.alpha = T(0); a.beta = T(1); a.want_rate = 0; a.rate_wr = nullptr;
+        CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
+        a.src = A; a.dst = B; a.alpha = T(0.75); a.beta = T(0.25);
+        CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
+        a.src = B; a.dst = U; a.alpha = T(1.0 / 3.0); a.beta = T(2.0 / 3.0); a.rate_wr = wr; a.want_rate = 1;
+        CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
+    }
+    CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)g->U, g->staging, s));
+    CUDA_TRY(cudaMemcpyAsync(out + p0, g->staging + p0, sizeof(double) * (p1 - p0), cudaMemcpyDeviceToHost, s));
+    g->launches += 3 + 3ull * nsteps;
+    return ROEAM_OK;
+}
+
+}  // namespace
+
 namespace roeam {
 // Records a message for roeam_last_error() from the other host translation units.
 int record_error(int status, const char *msg)
@@ -690,6 +739,10 @@ void roeam_destroy_grid(roeam_grid *g)
     if (g->h_rate) cudaFreeHost(g->h_rate);
     if (g->ev) cudaEventDestroy(g->ev);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    for (int k = 0; k < 2; ++k)
+        if (g->pipe[k]) cudaStreamDestroy(g->pipe[k]);
+    for (int k = 0; k < 3; ++k)
+        if (g->pipe_ev[k]) cudaEventDestroy(g->pipe_ev[k]);
     delete g;
 }
 
@@ -976,6 +1029,69 @@ roeam_status roeam_math_check(int device, int n, const double *x, double *out)
     cudaFree(dout);
     if (e != cudaSuccess) return fail(ROEAM_E_CUDA, "math check: %s", cudaGetErrorString(e));
     return ROEAM_OK;
+}
+
+roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const double *cons_in,
+                             double *cons_out, double *dt_last)
+{
+    if (!g || !cons_in || !cons_out) return fail(ROEAM_E_ARG, "null argument");
+    if (nsteps < 1) return fail(ROEAM_E_ARG, "nsteps must be >= 1");
+    if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(ROEAM_E_ARG, "need cfl > 0 or dt_fixed > 0");
+    if (!std::isfinite(cfl) || !std::isfinite(dt_fixed)) return fail(ROEAM_E_ARG, "cfl and dt_fixed must be finite");
+    if (g->stage_next != 0) return fail(ROEAM_E_STATE, "a step run by roeam_rk_stage is unfinished");
+    CUDA_TRY(cudaSetDevice(g->device));
+    for (int k = 0; k < 2; ++k)
+        if (!g->pipe[k]) CUDA_TRY(cudaStreamCreateWithFlags(&g->pipe[k], cudaStreamNonBlocking));
+    for (int k = 0; k < 3; ++k)
+        if (!g->pipe_ev[k]) CUDA_TRY(cudaEventCreateWithFlags(&g->pipe_ev[k], cudaEventDisableTiming));
+    // (the copy engines carry the host data: pack / unpack kernels reading and writing the
+    //  page-locked arrays in place measured slower)
+    // both pipeline streams start after the work already queued on the handle's stream
+    CUDA_TRY(cudaEventRecord(g->pipe_ev[2], g->stream));
+    for (int k = 0; k < 2; ++k) CUDA_TRY(cudaStreamWaitEvent(g->pipe[k], g->pipe_ev[2], 0));
+    // chunks of about 1/8 of the cells (whole grids), alternating between the two streams
+    const long long target = std::max(1ll, g->total_packed / 8);
+    int lo = 0, c = 0;
+    while (lo < g->count) {
+        int hi = lo + 1;
+        while (hi < g->count && g->hg[hi].poff - g->hg[lo].poff < target) ++hi;
+        roeam_status st = g->precision == 32
+                              ? pipe_chunk<float>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, g->pipe[c & 1])
+                              : pipe_chunk<double>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, g->pipe[c & 1]);
+        if (st != ROEAM_OK) return st;
+        lo = hi;
+        ++c;
+    }
+    for (int k = 0; k < 2; ++k) {
+        CUDA_TRY(cudaEventRecord(g->pipe_ev[k], g->pipe[k]));
+        CUDA_TRY(cudaStreamWaitEvent(g->stream, g->pipe_ev[k], 0));
+    }
+    for (int k = 0; k < g->count; ++k) g->state_set[k] = 1;
+    const long long step0 = g->step;
+    g->step += nsteps;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (dt_last) {
+        if (dt_fixed > 0.0) {
+            for (int k = 0; k < g->count; ++k) dt_last[k] = dt_fixed;
+        } else {
+            const int par = (int)((step0 + nsteps - 1) & 1);
+            CUDA_TRY(cudaMemcpy(g->h_rate, g->rate + (size_t)par * g->count, sizeof(unsigned long long) * g->count,
+                                cudaMemcpyDeviceToHost));
+            for (int k = 0; k < g->count; ++k) {
+                if (g->precision == 32) {
+                    float f;
+                    const uint32_t lo32 = (uint32_t)(g->h_rate[k] & 0xffffffffull);
+                    std::memcpy(&f, &lo32, sizeof(float));
+                    dt_last[k] = (double)(float(cfl) / f);
+                } else {
+                    double r;
+                    std::memcpy(&r, g->h_rate + k, sizeof(double));
+                    dt_last[k] = cfl / r;
+                }
+            }
+        }
+    }
+    return read_status(g);
 }
 
 }  // extern "C"

@@ -27,6 +27,7 @@ EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_
            "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
            "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc",
            "roeam_rk_stage", "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check",
+           "roeam_step_host",
            "roeam3_create_grid", "roeam3_destroy_grid", "roeam3_set_state", "roeam3_get_state",
            "roeam3_flux_residual", "roeam3_rk_step", "roeam3_conserved_totals", "roeam3_check",
            "roeam3_launch_count"]
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_flux_residual_noalloc.argtypes = [vp, C.c_int, vp]
     lib.roeam_rk_stage.argtypes = [vp, C.c_int, C.c_double]
     lib.roeam_math_check.argtypes = [C.c_int, C.c_int, dp, dp]
+    lib.roeam_step_host.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp, vp]
     lib.roeam_max_rate.argtypes = [vp, dp]
     lib.roeam_edge_rows.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
     lib.roeam_set_halo.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
@@ -110,7 +112,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
                  "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam_rk_stage",
-                 "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check", "roeam3_create_grid",
+                 "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check", "roeam_step_host",
+                 "roeam3_create_grid",
                  "roeam3_set_state", "roeam3_get_state", "roeam3_flux_residual", "roeam3_rk_step",
                  "roeam3_conserved_totals", "roeam3_check"):
         getattr(lib, name).restype = C.c_int
@@ -216,6 +219,12 @@ def roeam_autotune(h: int, cfl: float = 0.5, steps: int = 3):
     _check(load_library().roeam_autotune(C.c_void_p(h), cfl, steps, C.byref(best),
                                          ms.ctypes.data_as(C.POINTER(C.c_double))))
     return best.value, ms
+
+
+def roeam_step_host(h: int, cfl: float, dt_fixed: float, nsteps: int, cons_in, cons_out, dt_last=None) -> None:
+    _check(load_library().roeam_step_host(C.c_void_p(h), cfl, dt_fixed, nsteps, C.c_void_p(_ptr(cons_in)),
+                                          C.c_void_p(_ptr(cons_out)),
+                                          C.c_void_p(_ptr(dt_last) if dt_last is not None else None)))
 
 
 def roeam_math_check(x, device: int = 0) -> np.ndarray:

@@ -234,3 +234,31 @@ def test_batch_mixing_schemes(prec):
         Uo, dto = oracle.OracleGrid(s).step(U0[k], cfl=0.5)
         assert abs(dts[k] - dto) <= 1e-5 * dto
         assert rel_state_err(U1[k], Uo) <= TOL[prec], k
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_step_host_matches_separate_calls(prec):
+    """roeam_step_host (chunked, copies overlapped on two streams) gives exactly the state and
+    time steps of set_state + rk_step + get_state, for a batch spanning many chunks, with
+    page-locked and with pageable host arrays."""
+    import torch
+    specs, states = W.batch(40, seed=77)
+    packed = np.concatenate([s.ravel() for s in states])
+    h_in = torch.from_numpy(packed.copy()).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    dt_a = np.zeros(len(specs))
+    with P().Batch(specs, precision=prec) as b:
+        P().roeam_step_host(b.handle, 0.5, 0.0, 3, h_in, h_out, dt_a)
+        got = h_out.numpy().copy()
+        assert np.array_equal(np.concatenate([u.ravel() for u in b.get_states()]), got)
+    with P().Batch(specs, precision=prec) as b:
+        b.set_states(states)
+        dt_b = b.step(0.5, nsteps=3, want_dt=True)
+        ref = np.concatenate([u.ravel() for u in b.get_states()])
+    assert np.array_equal(got, ref)
+    assert np.array_equal(dt_a, dt_b)
+    # pageable host arrays; in place (cons_out = cons_in) is allowed
+    buf = packed.copy()
+    with P().Batch(specs, precision=prec) as b:
+        P().roeam_step_host(b.handle, 0.5, 0.0, 3, buf, buf)
+    assert np.array_equal(buf, ref)
