@@ -262,3 +262,16 @@ def test_step_host_matches_separate_calls(prec):
     with P().Batch(specs, precision=prec) as b:
         P().roeam_step_host(b.handle, 0.5, 0.0, 3, buf, buf)
     assert np.array_equal(buf, ref)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("shape", [(4, 4), (5, 7), (31, 4), (33, 5), (4, 65), (61, 6)])
+def test_tiny_and_tile_edge_grids(shape, prec):
+    """The smallest grids and sizes at the strip / segment edges (30 or 28 written columns per
+    strip, segments of 32 rows): periodic and wall/inflow/outflow, first order and van Leer."""
+    ni, nj = shape
+    for bc, recon in (((W.PERIODIC,) * 4, 0), ((W.INFLOW, W.OUTFLOW, W.WALL, W.WALL), 2)):
+        spec = W.GridSpec(ni=ni, nj=nj, dx=0.1, dy=0.1, bc=bc, inflow=(1.1, 0.4, 0.0, 1.0),
+                          params=W.SchemeParams(m_ref=0.4, recon=recon))
+        U = W.random_rough_state(spec, seed=ni * 100 + nj, mach=0.8, jump=0.3)
+        assert one_step_parity(spec, U, prec, cfl=0.4) <= TOL[prec], (bc, recon)
