@@ -281,9 +281,10 @@ def test_quirk_rotated_mach_number():
     """Section 7.2's printed number: with eps1 = 1, eps2 = 0.05 at eps_y = 0.1 and t ~ 100 the
     rotated Mach number f_rr / c on the faces parallel to x reaches about 1.73 on the perturbed
     centreline and near the shock and stays near zero in smooth flow. The time scheme and the
-    paper's domain differ (RK4, unstated), so only a loose range is checked: the maximum lies
-    in 1-2.5 and the median face is below 0.05. f_rr (Eqs. 103-109) is evaluated here from the
-    GPU state with the Roe averages, on the y-faces of the Cartesian part of the grid."""
+    paper's domain differ (RK4, unstated), so the range checked is loose: the maximum lies in
+    1.5-2 (measured: 1.733, near the shock) and the median face is below 0.05. f_rr (Eqs.
+    103-109) is evaluated here from the GPU state with the Roe averages, on the y-faces, with
+    the normal of the unperturbed grid."""
     spec, U = W.quirk(800, 20, eps_y=0.1, eps1=1)
     t = 0.0
     with P().Batch([spec], precision=32) as b:
@@ -308,5 +309,5 @@ def test_quirk_rotated_mach_number():
     U1 = n1x * uh + n1y * vh
     frr = np.abs(n1y * U1) + np.abs(vh - n1y * U1)        # |a1 U1| + |U - a1 U1| (Eq. 103)
     ratio = frr / ch
-    assert 1.0 <= ratio.max() <= 2.5, ratio.max()
+    assert 1.5 <= ratio.max() <= 2.0, ratio.max()
     assert np.median(ratio) < 0.05, np.median(ratio)
