@@ -277,8 +277,9 @@ def ablation_speed(P, torch, count=512, steps=50):
 def small_configs(P, torch):
     """The small paper-scale workloads, reported for latency (too small to load the HBM): the
     64^2 isentropic vortex (FP64, 100 steps), the 256^2 Gresho vortex at M = 0.01 (MUSCL
-    minmod, FP32 and FP64, 2000 steps) and the 800 x 20 Quirk duct (FP32, CFL 0.25, 4000 steps):
-    device ms per step through graph replays."""
+    minmod, FP32 and FP64, 2000 steps), the 800 x 20 Quirk duct (FP32, CFL 0.25, 4000 steps) and
+    the grids of Sections 7.3-7.6 (cylinder O-grid, blunt body, corner, wedge double-Mach
+    reflection): device ms per step through graph replays."""
     out = {}
     spec, U = W.isentropic_vortex(64)
     out["vortex_64_fp64"] = {"ms_per_step": time_single(P, torch, spec, U, 64, 100)[0], "steps": 100}
@@ -287,6 +288,16 @@ def small_configs(P, torch):
         out[f"gresho_256_fp{prec}"] = {"ms_per_step": time_single(P, torch, spec, U, prec, 2000)[0], "steps": 2000}
     spec, U = W.quirk(800, 20, eps_y=1e-6)
     out["quirk_800x20_fp32"] = {"ms_per_step": time_single(P, torch, spec, U, 32, 4000, cfl=0.25)[0], "steps": 4000}
+    # the Section 7.3-7.6 grids (FP32, first order; the hypersonic and shock cases at a fixed
+    # small dt so that the impulsive start needs no CFL ramp)
+    for name, (spec, U), steps, kw in (
+            ("cylinder_ogrid_100x72_fp32", W.cylinder_ogrid(mach=0.1), 2000, dict()),
+            ("blunt_body_160x20_fp32", W.cylinder_blunt(), 2000, dict(dt_fixed=1e-5)),
+            ("corner_400x400_fp32", W.supersonic_corner(400), 500, dict(dt_fixed=2e-5)),
+            ("wedge_dmr_800x200_fp32", W.wedge_dmr(800, 200), 500, dict(dt_fixed=2e-5))):
+        ms = time_single(P, torch, spec, U, 32, steps, **kw)[0]
+        out[name] = {"ms_per_step": ms, "steps": steps,
+                     "gcell_updates_per_s_per_stage": spec.ncells * 3 / (ms * 1e-3) / 1e9}
     return out
 
 
