@@ -98,21 +98,34 @@ struct roeam_grid {
 namespace {
 
 // Work units of the stage kernel for shape `cfg`: every grid is cut into strips of
-// 32 - 2H interior columns and into ceil(nj / ty) segments of nearly equal height. Units are
-// stored grouped by grid (for launches over one grid) and, for whole-batch launches, ordered
-// by decreasing height so that the static round-robin over warps stays balanced.
+// 32 - 2H interior columns and into ceil(nj / ty) segments of nearly equal height. A batch
+// too small to give every resident warp a unit (a single grid of a few thousand cells, like
+// the paper's test cases) gets shorter segments, down to 4 rows: each segment re-reads H + 1
+// rows above its first, but the rows are swept by many more warps at once. Units are stored
+// grouped by grid (for launches over one grid) and, for whole-batch launches, ordered by
+// decreasing height so that the static round-robin over warps stays balanced.
 roeam_status setup_tiles(roeam_grid *g, int cfg)
 {
     const TileCfg tc = TILE_CFGS[cfg];
     g->tile_cfg = cfg;
     const int H = g->muscl ? 2 : 1;
     const int width = tc.tx - 2 * H;
+    const int occ = g->precision == 32 ? Launchers<float>::stage_occupancy(g->muscl, g->curv, g->kind)
+                                       : Launchers<double>::stage_occupancy(g->muscl, g->curv, g->kind);
+    const long long warps = (long long)std::max(1, occ) * g->num_sms;
+    int ty = tc.ty;
+    for (;;) {
+        long long units = 0;
+        for (const GridDev &G : g->hg) units += (long long)((G.ni + width - 1) / width) * ((G.nj + ty - 1) / ty);
+        if (units >= warps || ty <= 4) break;
+        ty = std::max(4, ty / 2);
+    }
     std::vector<int4> ug;
     g->h_tile_base.assign(g->count + 1, 0);
     for (int k = 0; k < g->count; ++k) {
         GridDev &G = g->hg[k];
         G.ntx = (G.ni + width - 1) / width;
-        G.nty = (G.nj + tc.ty - 1) / tc.ty;
+        G.nty = (G.nj + ty - 1) / ty;
         G.ntiles = G.ntx * G.nty;
         G.tile_base = (int)ug.size();
         g->h_tile_base[k] = G.tile_base;
@@ -139,8 +152,6 @@ roeam_status setup_tiles(roeam_grid *g, int cfg)
     CUDA_TRY(cudaMemcpyAsync(g->d_units_grid, ug.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaMemcpyAsync(g->d_units_all, ua.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    const int occ = g->precision == 32 ? Launchers<float>::stage_occupancy(g->muscl, g->curv, g->kind)
-                                       : Launchers<double>::stage_occupancy(g->muscl, g->curv, g->kind);
     g->nblocks = std::max(1, occ * g->num_sms);
     for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
     g->graphs.clear();
