@@ -463,21 +463,23 @@ __device__ __forceinline__ FS<V> side_rot(V r, V u, V v, V p, V nx, V ny, const 
     return side_from_prims(r, vfma(nx, u, ny * v), vfma(nx, v, -(ny * u)), p, K);
 }
 
-// Reconstructed (or first-order) face states of one face in the global frame, with the
-// positivity fallback; returns false when an FP32 value within rounding of zero needs the
-// FP64 decision (taken here) — the caller is then on the scalar path anyway.
+// Reconstructed face states of one face in the global frame (packed path). Both limiters
+// keep a reconstructed value between the two cells of the face (minmod: within half the
+// smaller slope; van Leer: the harmonic mean is below twice either slope), so positive density
+// and pressure stay positive. The packed path runs only on faces whose two cells' densities
+// and pressures are within a factor 1e5 of each other, where that bound holds in FP32 with a
+// wide margin (rounding moves a value by a few ulps of the larger cell value, far less than the
+// smaller one); the positivity fallback to first order therefore never fires here, and the
+// scalar path keeps it for every other face.
 template <typename V, typename S>
 __device__ __forceinline__ void muscl_states(bool vanleer, const V Am[4], const V A[4], const V B[4], const V Bp[4],
                                              V WL[4], V WR[4])
 {
-    const V half = splat<V>(S(0.5)), zero = splat<V>(0);
-    V rL[4], rR[4];
+    const V half = splat<V>(S(0.5));
     for (int k = 0; k < 4; ++k) {
-        rL[k] = vfma(half, limiter(vanleer, A[k] - Am[k], B[k] - A[k]), A[k]);
-        rR[k] = B[k] - half * limiter(vanleer, B[k] - A[k], Bp[k] - B[k]);
+        WL[k] = vfma(half, limiter(vanleer, A[k] - Am[k], B[k] - A[k]), A[k]);
+        WR[k] = B[k] - half * limiter(vanleer, B[k] - A[k], Bp[k] - B[k]);
     }
-    const auto pos = gt(rL[0], zero) && gt(rL[3], zero) && gt(rR[0], zero) && gt(rR[3], zero);
-    for (int k = 0; k < 4; ++k) { WL[k] = sel(pos, rL[k], A[k]); WR[k] = sel(pos, rR[k], B[k]); }
 }
 
 // Scalar evaluation of one face: walls (first-order state and its mirror), MUSCL with solid
@@ -602,6 +604,14 @@ template <typename T> struct GridRegs {
     int bcW, bcE, bcS, bcN;
 };
 
+// Cell loads of the reconstructing kernels carry the L1 priority evict_last: their window is
+// deeper, so a row is read again by the stage epilogue several rows after its first load, and
+// without the hint most of those reads missed L1 (measured faster on the Cartesian and the
+// curvilinear reconstructing workloads; the first-order kernels measured slower with it).
+__device__ __forceinline__ float ld_keep(const float *p) { float v; asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p)); return v; }
+__device__ __forceinline__ double ld_keep(const double *p) { double v; asm("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p)); return v; }
+template <bool KEEP, typename T> __device__ __forceinline__ T ld_row(const T *p) { if constexpr (KEEP) return ld_keep(p); else return __ldg(p); }
+
 // Loading a cell is split in two so that the next row's HBM loads are in flight while the
 // current row is computed: issue_cell resolves row j (the column is resolved once per unit
 // into isrc / kx) and starts the loads; finish_cell turns them into primitives, derived face
@@ -612,22 +622,30 @@ template <typename T> struct GridRegs {
 template <typename T> struct Pending {
     T raw[4];
     int jsrc, ky;
+    int solid;   // the cell's solid-mask byte (kernels with walls)
 };
 
-template <typename T>
+template <typename T, bool WALLS, bool KEEP = false>
 __device__ __forceinline__ void issue_cell(const GridRegs<T> &R, int isrc, int kx, int j, Pending<T> &q)
 {
     q.jsrc = resolve_index(j, R.nj, R.bcS, R.bcN, q.ky);
+    q.solid = 0;
     if (kx != 2 && q.ky != 2) {
         const int x = q.jsrc * R.pitch + isrc;
-        q.raw[0] = __ldg(R.src + x);
-        q.raw[1] = __ldg(R.src + x + R.plane);
-        q.raw[2] = __ldg(R.src + x + 2 * R.plane);
-        q.raw[3] = __ldg(R.src + x + 3 * R.plane);
+        q.raw[0] = ld_row<KEEP>(R.src + x);
+        q.raw[1] = ld_row<KEEP>(R.src + x + R.plane);
+        q.raw[2] = ld_row<KEEP>(R.src + x + 2 * R.plane);
+        q.raw[3] = ld_row<KEEP>(R.src + x + 3 * R.plane);
+        // (grids with solid cells have no EXCHANGE side, so jsrc is a grid row here)
+        if constexpr (WALLS)
+            if (R.solid) q.solid = __ldg(R.solid + q.jsrc * R.ni + isrc);
     }
 }
 
-template <typename T, bool MUSCL, bool CURV, bool WALLS>
+// LATE_SOLID reads the solid-mask byte here instead of taking the one issue_cell prefetched
+// (the ablation kernels, whose scalar path measured faster that way; the main kernels hide
+// that load's latency behind a row of work).
+template <typename T, bool MUSCL, bool CURV, bool WALLS, bool LATE_SOLID = false>
 __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef<T> &K, int i, int isrc, int kx, int j,
                                             const Pending<T> &q, WC<T> &c)
 {
@@ -640,8 +658,8 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
         c.r = q.raw[0]; c.u = q.raw[1] * ri; c.v = q.raw[2] * ri;
         c.p = K.gm1 * (q.raw[3] - T(0.5) * q.raw[0] * (c.u * c.u + c.v * c.v));
         if constexpr (WALLS) {
-            // (grids with solid cells have no EXCHANGE side, so jsrc is a grid row here)
-            if (R.solid && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1;
+            if constexpr (LATE_SOLID) { if (R.solid && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1; }
+            else if (q.solid) c.fl = 1;
         }
     }
     if constexpr (WALLS) {
@@ -763,15 +781,18 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             }
             return ratio_P(lo.r, lo.p, hi.r, hi.p);
         };
+        // window rows j0-H .. j0+1, each row's loads issued one row ahead (the last issue is
+        // the loop's first prefetch, row j0+2)
+        for (int v = 0; v < NV; ++v) vload(j0 - 1 + v, vX[v], vY[v]);
+        issue_cell<T, WALLS && !ABL, MUSCL>(R, isrc, kx, j0 - H, pend);
         for (int w = 0; w < NW; ++w) {
             const int jr = j0 - H + w;
-            issue_cell(R, isrc, kx, jr, pend);
-            finish_cell<T, MUSCL, CURV, WALLS>(R, K, i, isrc, kx, jr, pend, Wn[w]);
+            const Pending<T> cur = pend;
+            issue_cell<T, WALLS && !ABL, MUSCL>(R, isrc, kx, jr + 1, pend);
+            finish_cell<T, MUSCL, CURV, WALLS, ABL>(R, K, i, isrc, kx, jr, cur, Wn[w]);
             Px[w] = px_of(Wn[w]);
             if (w > 0) Py[w - 1] = py_of(Wn[w - 1], Wn[w]);
         }
-        for (int v = 0; v < NV; ++v) vload(j0 - 1 + v, vX[v], vY[v]);
-        issue_cell(R, isrc, kx, j0 + 2, pend);
         T Un[4] = {T(0), T(0), T(0), T(0)};
         T acc[4] = {T(0), T(0), T(0), T(0)};
         T my_rate = T(0);
@@ -831,19 +852,10 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 fy.len = sqrt0(sx * sx + sy * sy);
                 li = rcp(fy.len);
                 fy.nx = sx * li; fy.ny = sy * li;
-                if constexpr (MUSCL) {
-                    // normals of the faces Am|A and B|Bp of both faces (mirrors at solid cells)
-                    fx.nAmx = shup(fx.nx, 1); fx.nAmy = shup(fx.ny, 1);
-                    fx.nBpx = shdn(fx.nx, 1); fx.nBpy = shdn(fx.ny, 1);
-                    const T x0 = shdn(vX[0], 1), y0 = shdn(vY[0], 1), x3 = shdn(vX[3], 1), y3 = shdn(vY[3], 1);
-                    T tx = -(y0 - vY[0]), ty = K.dx + (x0 - vX[0]), l = rsq(tx * tx + ty * ty);
-                    fy.nAmx = tx * l; fy.nAmy = ty * l;
-                    tx = -(y3 - vY[3]); ty = K.dx + (x3 - vX[3]); l = rsq(tx * tx + ty * ty);
-                    fy.nBpx = tx * l; fy.nBpy = ty * l;
-                } else {
+                if constexpr (!MUSCL) {
                     fx.nAmx = fx.nBpx = fx.nx; fx.nAmy = fx.nBpy = fx.ny;
                     fy.nAmx = fy.nBpx = fy.nx; fy.nAmy = fy.nBpy = fy.ny;
-                }
+                }   // (reconstructing: set on the scalar path, the only one that reads them)
             } else {
                 fx.nx = T(1); fx.ny = T(0); fx.len = K.dy;
                 fy.nx = T(0); fy.ny = T(1); fy.len = K.dx;
@@ -858,20 +870,30 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             if constexpr (PACKED && WALLS && !ABL)
                 scalar = __any_sync(0xffffffffu, face_is_wall(fx, MUSCL) || face_is_wall(fy, MUSCL));
             if constexpr (PACKED && MUSCL) {
-                // an FP32 reconstruction within rounding of zero is decided in FP64 (scalar path)
+                // faces across a density or pressure jump of 1e5 or more take the scalar path,
+                // where a reconstruction within rounding of zero is decided in FP64 (the
+                // reconstruction's bounds depend only on the face's two cells)
                 if (!scalar) {
                     const T eps = T(1e-5);
                     const bool marginal =
                         (fx.A.r < eps * fx.B.r) || (fx.B.r < eps * fx.A.r) || (fx.A.p < eps * fx.B.p) ||
                         (fx.B.p < eps * fx.A.p) || (fy.A.r < eps * fy.B.r) || (fy.B.r < eps * fy.A.r) ||
-                        (fy.A.p < eps * fy.B.p) || (fy.B.p < eps * fy.A.p) || (fx.Am.p < eps * fx.A.p) ||
-                        (fx.Bp.p < eps * fx.B.p) || (fy.Am.p < eps * fy.A.p) || (fy.Bp.p < eps * fy.B.p) ||
-                        (fx.Am.r < eps * fx.A.r) || (fx.Bp.r < eps * fx.B.r) || (fy.Am.r < eps * fy.A.r) ||
-                        (fy.Bp.r < eps * fy.B.r);
+                        (fy.A.p < eps * fy.B.p) || (fy.B.p < eps * fy.A.p);
                     scalar = __any_sync(0xffffffffu, marginal);
                 }
             }
             if (scalar) {
+                if constexpr (CURV && MUSCL) {
+                    // normals of the faces Am|A and B|Bp of both faces (mirrors at solid cells;
+                    // the branch is warp-uniform, so the shuffles are safe here)
+                    fx.nAmx = shup(fx.nx, 1); fx.nAmy = shup(fx.ny, 1);
+                    fx.nBpx = shdn(fx.nx, 1); fx.nBpy = shdn(fx.ny, 1);
+                    const T x0 = shdn(vX[0], 1), y0 = shdn(vY[0], 1), x3 = shdn(vX[3], 1), y3 = shdn(vY[3], 1);
+                    T tx = -(y0 - vY[0]), ty = K.dx + (x0 - vX[0]), l = rsq(tx * tx + ty * ty);
+                    fy.nAmx = tx * l; fy.nAmy = ty * l;
+                    tx = -(y3 - vY[3]); ty = K.dx + (x3 - vX[3]); l = rsq(tx * tx + ty * ty);
+                    fy.nBpx = tx * l; fy.nBpy = ty * l;
+                }
                 if constexpr (!PACKED || WALLS || MUSCL) {
                     face_scalar<T, MUSCL, ABL>(fx, K, eps1, xi_form, vanleer, Fw, var);
                     face_scalar<T, MUSCL, ABL>(fy, K, eps1, xi_form, vanleer, Fs, var);
@@ -933,10 +955,10 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             // ---- advance the window: row j+2 enters from the prefetch
             for (int w = 0; w < NW - 1; ++w) { Wn[w] = Wn[w + 1]; Px[w] = Px[w + 1]; }
             for (int w = 0; w < NW - 2; ++w) Py[w] = Py[w + 1];
-            finish_cell<T, MUSCL, CURV, WALLS>(R, K, i, isrc, kx, j + 2, pend, Wn[NW - 1]);
+            finish_cell<T, MUSCL, CURV, WALLS, ABL>(R, K, i, isrc, kx, j + 2, pend, Wn[NW - 1]);
             Px[NW - 1] = px_of(Wn[NW - 1]);
             Py[NW - 2] = py_of(Wn[NW - 2], Wn[NW - 1]);
-            issue_cell(R, isrc, kx, j + 3, pend);
+            issue_cell<T, WALLS && !ABL, MUSCL>(R, isrc, kx, j + 3, pend);
             if constexpr (CURV) {
                 for (int v = 0; v < NV - 1; ++v) { vX[v] = vX[v + 1]; vY[v] = vY[v + 1]; }
                 vload(j + 3, vX[NV - 1], vY[NV - 1]);
