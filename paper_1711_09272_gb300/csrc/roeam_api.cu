@@ -59,8 +59,10 @@ struct roeam_grid {
     int device = 0;
     cudaStream_t stream = nullptr;       // user stream (work is ordered on it)
     cudaStream_t cap_stream = nullptr;   // private stream used only for graph capture
-    cudaStream_t pipe[2] = {nullptr, nullptr};   // roeam_step_host: chunks alternate between them
-    cudaEvent_t pipe_ev[3] = {nullptr, nullptr, nullptr};
+    // roeam_step_host: streams for the copies in, the computation and the copies out, and
+    // events (the start, then two per chunk: copied in, computed)
+    cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> pipe_ev;
     int precision = 32, muscl = 0, curv = 0, kind = KIND_PLAIN, count = 0;   // kind: StageKind
     size_t esize = 4;
     int tile_cfg = 0;
@@ -94,6 +96,11 @@ struct roeam_grid {
     unsigned long long launches = 0;
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
+
+// roeam_step_host cuts the batch into about this many chunks (whole grids each).
+#ifndef ROEAM_PIPE_CHUNKS
+#define ROEAM_PIPE_CHUNKS 8
+#endif
 
 namespace {
 
@@ -525,15 +532,22 @@ void *stage_source(roeam_grid *g, int stage) { return stage == 0 ? g->U : (stage
 
 namespace {
 
-// One chunk of roeam_step_host: grids [lo, hi) from the packed host input to the packed host
-// output through nsteps steps, all on stream s (steps use the per-grid unit table).
+// One chunk of roeam_step_host, grids [lo, hi): the host-to-device copy of its packed input on
+// the copy-in stream, the computation (pack, rate, nsteps steps with the per-grid unit table,
+// unpack) on the compute stream once the copy has landed, and the device-to-host copy on the
+// copy-out stream once the computation is done. Chunks touch disjoint ranges of the staging
+// buffer, the state planes, the rate slots and the host arrays, so the three streams never
+// wait for one another except through the chunk's own two events.
 template <typename T>
 roeam_status pipe_chunk(roeam_grid *g, int lo, int hi, int nsteps, double cfl, double dt_fixed, const double *in,
-                        double *out, cudaStream_t s)
+                        double *out, cudaEvent_t copied, cudaEvent_t computed)
 {
+    cudaStream_t s_in = g->pipe[0], s = g->pipe[1], s_out = g->pipe[2];
     const long long p0 = g->hg[lo].poff;
     const long long p1 = hi < g->count ? g->hg[hi].poff : g->total_packed;
-    CUDA_TRY(cudaMemcpyAsync(g->staging + p0, in + p0, sizeof(double) * (p1 - p0), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(g->staging + p0, in + p0, sizeof(double) * (p1 - p0), cudaMemcpyHostToDevice, s_in));
+    CUDA_TRY(cudaEventRecord(copied, s_in));
+    CUDA_TRY(cudaStreamWaitEvent(s, copied, 0));
     CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, g->staging, (T *)g->U, s));
     unsigned long long *slot0 = g->rate + (size_t)(g->step & 1) * g->count;
     CUDA_TRY(cudaMemsetAsync(slot0 + lo, 0, sizeof(unsigned long long) * (hi - lo), s));
@@ -563,7 +577,9 @@ roeam_status pipe_chunk(roeam_grid *g, int lo, int hi, int nsteps, double cfl, d
         CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
     }
     CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)g->U, g->staging, s));
-    CUDA_TRY(cudaMemcpyAsync(out + p0, g->staging + p0, sizeof(double) * (p1 - p0), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaEventRecord(computed, s));
+    CUDA_TRY(cudaStreamWaitEvent(s_out, computed, 0));
+    CUDA_TRY(cudaMemcpyAsync(out + p0, g->staging + p0, sizeof(double) * (p1 - p0), cudaMemcpyDeviceToHost, s_out));
     g->launches += 3 + 3ull * nsteps;
     return ROEAM_OK;
 }
@@ -750,10 +766,9 @@ void roeam_destroy_grid(roeam_grid *g)
     if (g->h_rate) cudaFreeHost(g->h_rate);
     if (g->ev) cudaEventDestroy(g->ev);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
-    for (int k = 0; k < 2; ++k)
-        if (g->pipe[k]) cudaStreamDestroy(g->pipe[k]);
     for (int k = 0; k < 3; ++k)
-        if (g->pipe_ev[k]) cudaEventDestroy(g->pipe_ev[k]);
+        if (g->pipe[k]) cudaStreamDestroy(g->pipe[k]);
+    for (cudaEvent_t e : g->pipe_ev) cudaEventDestroy(e);
     delete g;
 }
 
@@ -1051,32 +1066,38 @@ roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nst
     if (!std::isfinite(cfl) || !std::isfinite(dt_fixed)) return fail(ROEAM_E_ARG, "cfl and dt_fixed must be finite");
     if (g->stage_next != 0) return fail(ROEAM_E_STATE, "a step run by roeam_rk_stage is unfinished");
     CUDA_TRY(cudaSetDevice(g->device));
-    for (int k = 0; k < 2; ++k)
-        if (!g->pipe[k]) CUDA_TRY(cudaStreamCreateWithFlags(&g->pipe[k], cudaStreamNonBlocking));
     for (int k = 0; k < 3; ++k)
-        if (!g->pipe_ev[k]) CUDA_TRY(cudaEventCreateWithFlags(&g->pipe_ev[k], cudaEventDisableTiming));
-    // (the copy engines carry the host data: pack / unpack kernels reading and writing the
-    //  page-locked arrays in place measured slower)
-    // both pipeline streams start after the work already queued on the handle's stream
-    CUDA_TRY(cudaEventRecord(g->pipe_ev[2], g->stream));
-    for (int k = 0; k < 2; ++k) CUDA_TRY(cudaStreamWaitEvent(g->pipe[k], g->pipe_ev[2], 0));
-    // chunks of about 1/8 of the cells (whole grids), alternating between the two streams
-    const long long target = std::max(1ll, g->total_packed / 8);
-    int lo = 0, c = 0;
-    while (lo < g->count) {
+        if (!g->pipe[k]) CUDA_TRY(cudaStreamCreateWithFlags(&g->pipe[k], cudaStreamNonBlocking));
+    // chunks of about 1/ROEAM_PIPE_CHUNKS of the cells (whole grids)
+    const long long target = std::max(1ll, g->total_packed / ROEAM_PIPE_CHUNKS);
+    std::vector<std::pair<int, int>> chunks;
+    for (int lo = 0; lo < g->count;) {
         int hi = lo + 1;
         while (hi < g->count && g->hg[hi].poff - g->hg[lo].poff < target) ++hi;
-        roeam_status st = g->precision == 32
-                              ? pipe_chunk<float>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, g->pipe[c & 1])
-                              : pipe_chunk<double>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, g->pipe[c & 1]);
-        if (st != ROEAM_OK) return st;
+        chunks.emplace_back(lo, hi);
         lo = hi;
-        ++c;
     }
-    for (int k = 0; k < 2; ++k) {
-        CUDA_TRY(cudaEventRecord(g->pipe_ev[k], g->pipe[k]));
-        CUDA_TRY(cudaStreamWaitEvent(g->stream, g->pipe_ev[k], 0));
+    while (g->pipe_ev.size() < 1 + 2 * chunks.size()) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g->pipe_ev.push_back(e);
     }
+    // (the copy engines carry the host data: pack / unpack kernels reading and writing the
+    //  page-locked arrays in place measured slower)
+    // the three streams start after the work already queued on the handle's stream
+    CUDA_TRY(cudaEventRecord(g->pipe_ev[0], g->stream));
+    for (int k = 0; k < 3; ++k) CUDA_TRY(cudaStreamWaitEvent(g->pipe[k], g->pipe_ev[0], 0));
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        const int lo = chunks[c].first, hi = chunks[c].second;
+        cudaEvent_t copied = g->pipe_ev[1 + 2 * c], computed = g->pipe_ev[2 + 2 * c];
+        roeam_status st =
+            g->precision == 32 ? pipe_chunk<float>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, copied, computed)
+                               : pipe_chunk<double>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, copied, computed);
+        if (st != ROEAM_OK) return st;
+    }
+    // the handle's stream resumes after the last copy out (which follows every computation)
+    CUDA_TRY(cudaEventRecord(g->pipe_ev[0], g->pipe[2]));
+    CUDA_TRY(cudaStreamWaitEvent(g->stream, g->pipe_ev[0], 0));
     for (int k = 0; k < g->count; ++k) g->state_set[k] = 1;
     const long long step0 = g->step;
     g->step += nsteps;
