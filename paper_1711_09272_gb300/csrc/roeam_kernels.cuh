@@ -463,24 +463,18 @@ __device__ __forceinline__ FS<V> side_rot(V r, V u, V v, V p, V nx, V ny, const 
     return side_from_prims(r, vfma(nx, u, ny * v), vfma(nx, v, -(ny * u)), p, K);
 }
 
-// Reconstructed face states of one face in the global frame (packed path). Both limiters
-// keep a reconstructed value between the two cells of the face (minmod: within half the
-// smaller slope; van Leer: the harmonic mean is below twice either slope), so positive density
-// and pressure stay positive. The packed path runs only on faces whose two cells' densities
-// and pressures are within a factor 1e5 of each other, where that bound holds in FP32 with a
-// wide margin (rounding moves a value by a few ulps of the larger cell value, far less than the
-// smaller one); the positivity fallback to first order therefore never fires here, and the
-// scalar path keeps it for every other face.
-template <typename V, typename S>
-__device__ __forceinline__ void muscl_states(bool vanleer, const V Am[4], const V A[4], const V B[4], const V Bp[4],
-                                             V WL[4], V WR[4])
-{
-    const V half = splat<V>(S(0.5));
-    for (int k = 0; k < 4; ++k) {
-        WL[k] = vfma(half, limiter(vanleer, A[k] - Am[k], B[k] - A[k]), A[k]);
-        WR[k] = B[k] - half * limiter(vanleer, B[k] - A[k], Bp[k] - B[k]);
-    }
-}
+// Packed reconstruction. A face's left state is its left cell plus half that cell's limited
+// slope, its right state its right cell minus half that cell's slope, so the slope is a
+// per-cell quantity: a lane evaluates its cell's x- and y-slopes as one packed pair, takes the
+// west cell's x-slope from its neighbour lane and the south cell's y-slope from the row before
+// (the same operands, and so the same values, as evaluating both slopes per face). Both
+// limiters keep a reconstructed value between the two cells of the face (minmod: within half
+// the smaller slope; van Leer: the harmonic mean is below twice either slope), so positive
+// density and pressure stay positive. The packed path runs only on faces whose two cells'
+// densities and pressures are within a factor 1e5 of each other, where that bound holds in
+// FP32 with a wide margin (rounding moves a value by a few ulps of the larger cell value, far
+// less than the smaller one); the positivity fallback to first order therefore never fires
+// there, and the scalar path keeps it for every other face.
 
 // Scalar evaluation of one face: walls (first-order state and its mirror), MUSCL with solid
 // mirrors and the FP64 positivity decision in FP32, rotation to the face frame, flux, and the
@@ -536,10 +530,12 @@ __device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> 
 
 // Packed FP32 evaluation of a lane's x-face (component x) and y-face (component y), both free
 // of walls. Cartesian faces enter with their normal velocity first (the y-face's (v, u) is a
-// relabelling, undone on output); curvilinear faces are rotated by their normals.
+// relabelling, undone on output); curvilinear faces are rotated by their normals. WL / WR are
+// the reconstructed states (global frame) of the reconstructing kernels.
 template <bool MUSCL, bool CURV>
 __device__ __forceinline__ void faces_packed(const Face<float> &fx, const Face<float> &fy, const GridCoef<float> &K,
-                                             int eps1, int xi_form, bool vanleer, float Fx[4], float Fy[4])
+                                             int eps1, int xi_form, const V2 WL[4], const V2 WR[4], float Fx[4],
+                                             float Fy[4])
 {
     FS<V2> L, R;
     if constexpr (!MUSCL) {
@@ -558,12 +554,6 @@ __device__ __forceinline__ void faces_packed(const Face<float> &fx, const Face<f
                  mk2(b.sr, d.sr), mk2(b.Mq, d.Mq)};
         }
     } else {
-        const V2 Am[4] = {mk2(fx.Am.r, fy.Am.r), mk2(fx.Am.u, fy.Am.u), mk2(fx.Am.v, fy.Am.v), mk2(fx.Am.p, fy.Am.p)};
-        const V2 A[4] = {mk2(fx.A.r, fy.A.r), mk2(fx.A.u, fy.A.u), mk2(fx.A.v, fy.A.v), mk2(fx.A.p, fy.A.p)};
-        const V2 B[4] = {mk2(fx.B.r, fy.B.r), mk2(fx.B.u, fy.B.u), mk2(fx.B.v, fy.B.v), mk2(fx.B.p, fy.B.p)};
-        const V2 Bp[4] = {mk2(fx.Bp.r, fy.Bp.r), mk2(fx.Bp.u, fy.Bp.u), mk2(fx.Bp.v, fy.Bp.v), mk2(fx.Bp.p, fy.Bp.p)};
-        V2 WL[4], WR[4];
-        muscl_states<V2, float>(vanleer, Am, A, B, Bp, WL, WR);
         if constexpr (CURV) {
             const V2 nx = mk2(fx.nx, fy.nx), ny = mk2(fx.ny, fy.ny);
             L = side_rot(WL[0], WL[1], WL[2], WL[3], nx, ny, K);
@@ -793,6 +783,14 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             Px[w] = px_of(Wn[w]);
             if (w > 0) Py[w - 1] = py_of(Wn[w - 1], Wn[w]);
         }
+        // the y-slope of row j0 - 1 (packed reconstruction), as the loop would have left it
+        float sy_prev[4] = {0.f, 0.f, 0.f, 0.f};
+        if constexpr (PACKED && MUSCL) {
+            const WC<T> &a0 = Wn[H - 2], &b0 = Wn[H - 1], &c0 = Wn[H];
+            const V2 lo = limiter(vanleer, mk2(b0.r, b0.u) - mk2(a0.r, a0.u), mk2(c0.r, c0.u) - mk2(b0.r, b0.u));
+            const V2 hi = limiter(vanleer, mk2(b0.v, b0.p) - mk2(a0.v, a0.p), mk2(c0.v, c0.p) - mk2(b0.v, b0.p));
+            sy_prev[0] = lo.v.x; sy_prev[1] = lo.v.y; sy_prev[2] = hi.v.x; sy_prev[3] = hi.v.y;
+        }
         T Un[4] = {T(0), T(0), T(0), T(0)};
         T acc[4] = {T(0), T(0), T(0), T(0)};
         T my_rate = T(0);
@@ -818,7 +816,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             fy.A = Wn[H - 1];
             fy.B = Wn[H];
             if constexpr (MUSCL) {
-                fx.Am = shup_c<WALLS>(Wn[H], 2, false);
+                // (fx.Am's values are shuffled in on the scalar path, the only one that reads them)
+                fx.Am.fl = WALLS ? (uint8_t)__shfl_up_sync(0xffffffffu, (int)Wn[H].fl, 2) : (uint8_t)0;
                 fx.Bp = shdn_c<WALLS>(Wn[H], 1);
                 fy.Am = Wn[H - 2];
                 fy.Bp = Wn[H + 1];
@@ -863,6 +862,22 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 fy.nAmx = fy.nBpx = T(0); fy.nAmy = fy.nBpy = T(1);
             }
 
+            // per-cell limited slopes (packed reconstruction): this cell's (x, y) pair, the
+            // west cell's x-slope and the south cell's y-slope (carried from the row before)
+            V2 WLp[4], WRp[4];
+            if constexpr (PACKED && MUSCL) {
+                const float Ax[4] = {fx.A.r, fx.A.u, fx.A.v, fx.A.p}, Ay[4] = {fy.A.r, fy.A.u, fy.A.v, fy.A.p};
+                const float Bc[4] = {fx.B.r, fx.B.u, fx.B.v, fx.B.p};
+                const float Px_[4] = {fx.Bp.r, fx.Bp.u, fx.Bp.v, fx.Bp.p}, Py_[4] = {fy.Bp.r, fy.Bp.u, fy.Bp.v, fy.Bp.p};
+                const V2 half = mk2(0.5f, 0.5f);
+                for (int k = 0; k < 4; ++k) {
+                    const V2 A2 = mk2(Ax[k], Ay[k]), B2 = mk2(Bc[k], Bc[k]);
+                    const V2 sg = limiter(vanleer, B2 - A2, mk2(Px_[k], Py_[k]) - B2);
+                    WRp[k] = B2 - half * sg;
+                    WLp[k] = vfma(half, mk2(shup(sg.v.x, 1), sy_prev[k]), A2);
+                    sy_prev[k] = sg.v.y;
+                }
+            }
             T Fw[4], Fs[4];
             // walls, solid cells (and FP64, and the ablation variants) take the scalar path;
             // batches without walls or solid cells never do in FP32
@@ -883,6 +898,11 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 }
             }
             if (scalar) {
+                if constexpr (MUSCL) {
+                    const uint8_t fl = fx.Am.fl;
+                    fx.Am = shup_c<WALLS>(Wn[H], 2, false);
+                    fx.Am.fl = fl;
+                }
                 if constexpr (CURV && MUSCL) {
                     // normals of the faces Am|A and B|Bp of both faces (mirrors at solid cells;
                     // the branch is warp-uniform, so the shuffles are safe here)
@@ -899,7 +919,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     face_scalar<T, MUSCL, ABL>(fy, K, eps1, xi_form, vanleer, Fs, var);
                 }
             } else if constexpr (PACKED) {
-                faces_packed<MUSCL, CURV>(fx, fy, K, eps1, xi_form, vanleer, Fw, Fs);
+                faces_packed<MUSCL, CURV>(fx, fy, K, eps1, xi_form, WLp, WRp, Fw, Fs);
             }
             // (faces of lanes or rows outside the grid are computed from clamped or ghost states
             //  and never reach a written cell: a written cell's faces all lie in the grid)
