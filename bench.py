@@ -158,10 +158,21 @@ def reduce_max(value: float, world: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
-def weak_value(cells_per_rank: int, world: int, steps: int, ms: float) -> float:
-    """Whole-job Gcell-updates per second per RK stage: all ranks' cells x 3 stages x steps
-    over the slowest rank's time."""
-    return cells_per_rank * world * 3 * steps / (ms * 1e-3) / 1e9
+def reduce_sum(value: int, world: int, device: str = "cuda") -> int:
+    """Sum over ranks of a per-rank count (the cells of every rank's batch; reporting only)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
+def weak_value(total_cells: int, steps: int, ms: float) -> float:
+    """Whole-job Gcell-updates per second per RK stage: all ranks' cells (each rank its own
+    batch) x 3 stages x steps over the slowest rank's time."""
+    return total_cells * 3 * steps / (ms * 1e-3) / 1e9
 
 
 def cpu_baseline(specs, states, steps: int = 1, budget_s: float = 20.0):
@@ -420,7 +431,8 @@ def run_ours(args):
     launches = b.launches - l0
     b.check()
     ms = reduce_max(ms, world)
-    value = weak_value(ncells, world, args.steps, ms)
+    total_cells = reduce_sum(ncells, world)
+    value = weak_value(total_cells, args.steps, ms)
 
     # ---- per-launch duration of the stage kernel (events around single steps = 3 launches)
     per = []
@@ -446,7 +458,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             P.roeam_step_host(b.handle, 0.5, 0.0, 1, h_in, h_out)
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, world)
         # the same through three separate calls (copies not overlapped with the step)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -454,11 +466,12 @@ def run_ours(args):
             P.roeam_set_state(b.handle, -1, h_in)
             b.step(cfl=0.5, nsteps=1)
             P.roeam_get_state(b.handle, -1, h_out)
-        sep_s = (time.perf_counter() - t1) / e2e_steps
-        e2e = {"value": ncells * 3 / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": packed.nbytes,
-               "d2h_bytes_per_step": packed.nbytes,
+        sep_s = reduce_max((time.perf_counter() - t1) / e2e_steps, world)
+        e2e = {"value": total_cells * 3 / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": reduce_sum(packed.nbytes, world),
+               "d2h_bytes_per_step": reduce_sum(packed.nbytes, world),
                "path": "roeam_step_host(pinned fp64 in, pinned fp64 out, 1 step): chunked, copies overlapped",
-               "separate_calls": {"value": ncells * 3 / sep_s / 1e9,
+               "separate_calls": {"value": total_cells * 3 / sep_s / 1e9,
                                   "path": "roeam_set_state + roeam_rk_step(1) + roeam_get_state (pinned fp64)"}}
 
     line = None

@@ -27,7 +27,9 @@ def _worker(rank, world, port, out):
     import workloads as W
     specs, _ = W.batch(4, seed=bench.rank_seed(rank))
     ms = 10.0 + 5.0 * rank
-    out[rank] = (bench.reduce_max(ms, world, device="cpu"), [s.ni for s in specs], sum(s.ncells for s in specs))
+    cells = sum(s.ncells for s in specs)
+    out[rank] = (bench.reduce_max(ms, world, device="cpu"), [s.ni for s in specs], cells,
+                 bench.reduce_sum(cells, world, device="cpu"))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -37,13 +39,14 @@ def test_two_rank_weak_scaling_host_logic():
     mgr = mp.Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
-    t0, ni0, c0 = out[0]
-    t1, ni1, c1 = out[1]
+    t0, ni0, c0, tot0 = out[0]
+    t1, ni1, c1, tot1 = out[1]
     assert t0 == t1 == 15.0                 # both ranks report the slowest rank's time
     assert ni0 != ni1                       # independent batches per rank
+    assert tot0 == tot1 == c0 + c1          # the whole job's cells, whatever each rank drew
     import bench
-    v = bench.weak_value(c0, world, 10, t0)
-    assert v == pytest.approx(c0 * 2 * 3 * 10 / 15e-3 / 1e9)
+    v = bench.weak_value(tot0, 10, t0)
+    assert v == pytest.approx((c0 + c1) * 3 * 10 / 15e-3 / 1e9)
 
 
 # ----------------------------------------------------------------------------- row slabs
