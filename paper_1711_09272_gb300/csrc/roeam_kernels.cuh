@@ -501,13 +501,24 @@ __device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> 
             rR[k] = WR[k] - T(0.5) * lR[k];
         }
         // Positivity of the reconstructed density and pressure, else first order. In FP32 a
-        // value within rounding of zero is re-decided exactly in FP64.
+        // density or pressure that comes out within rounding of zero (or below it) is
+        // reconstructed again in FP64 from the same cell values and decided there: a limited
+        // reconstruction lies between the face's two cells, which FP32 cannot resolve across a
+        // jump of seven or more orders of magnitude, while FP64 decides as the FP64 path does.
         bool pos = rL[0] > T(0) && rL[3] > T(0) && rR[0] > T(0) && rR[3] > T(0);
-        if (sizeof(T) == 4 && pos) {
+        if constexpr (sizeof(T) == 4) {
             const T eps = T(1e-6);
-            if (rL[0] < eps * WL[0] || rL[3] < eps * WL[3] || rR[0] < eps * WR[0] || rR[3] < eps * WR[3])
-                pos = ((double)WL[0] + 0.5 * (double)lL[0] > 0.0) && ((double)WL[3] + 0.5 * (double)lL[3] > 0.0) &&
-                      ((double)WR[0] - 0.5 * (double)lR[0] > 0.0) && ((double)WR[3] - 0.5 * (double)lR[3] > 0.0);
+            if (!(rL[0] > eps * WL[0]) || !(rL[3] > eps * WL[3]) || !(rR[0] > eps * WR[0]) || !(rR[3] > eps * WR[3])) {
+                double dL[4], dR[4];
+                for (int k = 0; k < 4; ++k) {
+                    const double wl = WL[k], wr = WR[k], m0 = M0[k], m3 = M3[k];
+                    dL[k] = wl + 0.5 * limiter(vanleer, wl - m0, wr - wl);
+                    dR[k] = wr - 0.5 * limiter(vanleer, wr - wl, m3 - wr);
+                }
+                pos = dL[0] > 0.0 && dL[3] > 0.0 && dR[0] > 0.0 && dR[3] > 0.0;
+                if (pos)
+                    for (int k = 0; k < 4; ++k) { rL[k] = (T)dL[k]; rR[k] = (T)dR[k]; }
+            }
         }
         if (pos) for (int k = 0; k < 4; ++k) { WL[k] = rL[k]; WR[k] = rR[k]; }
     }

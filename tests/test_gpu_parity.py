@@ -115,6 +115,48 @@ def test_residual_parity(prec):
     assert err <= (1e-13 if prec == 64 else 2e-6), err
 
 
+def graded_state(spec, seed=11, drop=1e-8, mach=0.3):
+    """Density and pressure fall by `drop` from column to column (levels 1, drop, drop^2,
+    drop^3, repeating along i; factors 0.8-1.2), velocities at `mach` times the sound speed in
+    random directions."""
+    rng = np.random.default_rng(seed)
+    lev = np.broadcast_to(np.arange(spec.ni)[None, :] % 4, (spec.nj, spec.ni))
+    rho = drop ** lev * (0.8 + 0.4 * rng.random((spec.nj, spec.ni)))
+    p = drop ** lev * (0.8 + 0.4 * rng.random((spec.nj, spec.ni)))
+    c = np.sqrt(spec.params.gamma * p / rho)
+    th = 2 * np.pi * rng.random((spec.nj, spec.ni))
+    u, v = mach * c * np.cos(th), mach * c * np.sin(th)
+    E = p / (spec.params.gamma - 1) + 0.5 * rho * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, E])
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("recon", [1, 2])
+def test_residual_across_eight_orders_of_magnitude(prec, recon):
+    """A face whose upwind neighbour is 1e8 times heavier: van Leer's slope (up to twice the
+    smaller difference) reconstructs the face's left state to about the lighter cell's level,
+    which in FP32 lies within rounding of zero. The FP32 path must take the reconstruction (and
+    its positivity decision) as the FP64 path does: a first-order fallback there would put the
+    heavier cell's pressure on the face. Residuals are compared per cell against the flux scale
+    of the cell and its four face neighbours, so that a face at the 1e-8 level is not hidden
+    behind the heavy cells' fluxes."""
+    spec = W.GridSpec(ni=40, nj=12, dx=0.02, dy=0.02, params=W.SchemeParams(m_ref=0.3, recon=recon))
+    U = graded_state(spec)
+    with P().Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        U0 = b.get_state(0)
+        Rg = b.residual(0)
+    Ro = oracle.OracleGrid(spec).residual(U0)
+    rho, u, v, p = W.cons_to_prim(U0)
+    a = np.abs(u) + np.abs(v)
+    f = rho * a * a + p + (p * 3.5 + rho * (u * u + v * v)) * (a + 2)
+    local = np.maximum.reduce([f, np.roll(f, 1, 0), np.roll(f, -1, 0), np.roll(f, 1, 1), np.roll(f, -1, 1)])
+    scale = local * 4 / min(spec.dx, spec.dy)
+    err = np.max(np.abs(Rg - Ro) / scale[None])
+    assert np.all(np.isfinite(Rg))
+    assert err <= (1e-12 if prec == 64 else 1e-5), err
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_free_stream_exact(prec):
     spec = W.GridSpec(ni=70, nj=19, dx=0.1, dy=0.1, params=W.SchemeParams(recon=2, m_ref=0.1))
