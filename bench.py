@@ -454,12 +454,16 @@ def run_ours(args):
         h_in = torch.from_numpy(packed).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         e2e_steps = 5
+        P.roeam_step_host(b.handle, 0.5, 0.0, 1, h_in, h_out)   # untimed: creates the pipeline streams
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             P.roeam_step_host(b.handle, 0.5, 0.0, 1, h_in, h_out)
         e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, world)
         # the same through three separate calls (copies not overlapped with the step)
+        P.roeam_set_state(b.handle, -1, h_in)
+        b.step(cfl=0.5, nsteps=1)
+        P.roeam_get_state(b.handle, -1, h_out)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         for _ in range(e2e_steps):
