@@ -280,7 +280,7 @@ def test_batch_mixing_schemes(prec):
 
 @pytest.mark.parametrize("prec", [64, 32])
 def test_step_host_matches_separate_calls(prec):
-    """roeam_step_host (chunked, copies overlapped on two streams) gives exactly the state and
+    """roeam_step_host (chunked, copies in, steps and copies out on three streams) gives exactly the state and
     time steps of set_state + rk_step + get_state, for a batch spanning many chunks, with
     page-locked and with pageable host arrays."""
     import torch
