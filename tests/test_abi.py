@@ -79,3 +79,24 @@ def test_exchange_sides_are_validated():
     with pytest.raises(P.RoeamError) as e:
         P.roeam_create_grid([P.make_desc(spec)])
     assert "EXCHANGE" in str(e.value)
+
+
+def test_size_limits_are_validated():
+    """The largest handle holds 65535 grids of at most 2^28 cells each (the kernels index a
+    grid's planes with 32-bit offsets); one grid more, or one cell row more, is refused before
+    any device work."""
+    import workloads as W
+    import paper_1711_09272_gb300 as P
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam_create_grid([P.make_desc(W.GridSpec(ni=4, nj=4))] * 65536)
+    assert e.value.status == 1 and "65535" in str(e.value)
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam_create_grid([P.make_desc(W.GridSpec(ni=16384, nj=16385))])
+    assert e.value.status == 1 and "too many cells" in str(e.value)
+    # the 3D handle has the same limits
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam3_create_grid([P.make_desc3(W.GridSpec3(ni=4, nj=4, nk=4))] * 65536)
+    assert e.value.status == 1 and "65535" in str(e.value)
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam3_create_grid([P.make_desc3(W.GridSpec3(ni=1024, nj=1024, nk=257))])
+    assert e.value.status == 1 and "too many cells" in str(e.value)

@@ -102,6 +102,26 @@ def test_warped_step_full_size_sampled_parity():
     check_cells(spec, U0, U1, dt, cells, 1e-5)
 
 
+def test_largest_grid_sampled_parity():
+    """One grid of 2^28 cells (16384 x 16384, the largest a handle accepts; its planes are
+    addressed with 32-bit offsets), FP32, first order, inflow / outflow / walls: one step,
+    with the four corners, edge cells and random cells recomputed by the oracle."""
+    n = 16384
+    spec = W.GridSpec(ni=n, nj=n, dx=1.0 / n, dy=1.0 / n, bc=(W.INFLOW, W.OUTFLOW, W.WALL, W.WALL),
+                      inflow=(1.0, 0.6, 0.0, 1.0), params=W.SchemeParams(m_ref=0.5))
+    U = W.random_smooth_state(spec, seed=28, mach=0.5, amp=0.3)
+    with P().Batch([spec], precision=32) as b:
+        b.set_state(U, 0)
+        del U
+        U0 = b.get_state(0)
+        dt = b.step(0.5, nsteps=1, want_dt=True)[0]
+        U1 = b.get_state(0)
+    rng = W.SplitMix64(28)
+    cells = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (n // 2, 0), (n - 1, n // 2), (n // 2 - 1, n // 2)]
+    cells += [(int(rng.uniform() * n), int(rng.uniform() * n)) for _ in range(8)]
+    check_cells(spec, U0, U1, dt, cells, 1e-5)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_checkpoint_restart_is_bit_identical(prec):
     spec = W.with_params(W.warped_periodic(48, amp=0.15), recon=2)

@@ -317,3 +317,27 @@ def test_tiny_and_tile_edge_grids(shape, prec):
                           params=W.SchemeParams(m_ref=0.4, recon=recon))
         U = W.random_rough_state(spec, seed=ni * 100 + nj, mach=0.8, jump=0.3)
         assert one_step_parity(spec, U, prec, cfl=0.4) <= TOL[prec], (bc, recon)
+
+
+def test_largest_batch_count():
+    """A handle at its largest batch size, 65535 grids (4 to 7 cells a side, periodic or
+    wall/inflow/outflow, van Leer, FP32): one step of the whole batch, with every 1000th grid
+    and the last one recomputed by the oracle from the device's state."""
+    rng = np.random.default_rng(65535)
+    specs, states = [], []
+    for k in range(65535):
+        ni, nj = (int(x) for x in rng.integers(4, 8, size=2))
+        walls = k % 2 == 1
+        bc = (W.INFLOW, W.OUTFLOW, W.WALL, W.WALL) if walls else (W.PERIODIC,) * 4
+        spec = W.GridSpec(ni=ni, nj=nj, dx=0.1, dy=0.1, bc=bc, inflow=(1.1, 0.4, 0.0, 1.0),
+                          params=W.SchemeParams(m_ref=0.4, recon=2))
+        specs.append(spec)
+        states.append(W.random_rough_state(spec, seed=k, mach=0.8, jump=0.3))
+    with P().Batch(specs, precision=32) as b:
+        b.set_states(states)
+        U0 = b.get_states()
+        dts = b.step(0.4, nsteps=1, want_dt=True)
+        U1 = b.get_states()
+    for k in list(range(0, 65535, 1000)) + [65534]:
+        Uo, _ = oracle.OracleGrid(specs[k]).step(U0[k], dt_fixed=float(dts[k]))
+        assert rel_state_err(U1[k], Uo) <= TOL[32], k
