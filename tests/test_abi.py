@@ -84,9 +84,12 @@ def test_exchange_sides_are_validated():
 def test_size_limits_are_validated():
     """The largest handle holds 65535 grids of at most 2^28 cells each (the kernels index a
     grid's planes with 32-bit offsets); one grid more, or one cell row more, is refused before
-    any device work."""
+    any device work, and so is an empty batch."""
     import workloads as W
     import paper_1711_09272_gb300 as P
+    with pytest.raises(P.RoeamError) as e:
+        P.roeam_create_grid([])
+    assert e.value.status == 1 and "count" in str(e.value)
     with pytest.raises(P.RoeamError) as e:
         P.roeam_create_grid([P.make_desc(W.GridSpec(ni=4, nj=4))] * 65536)
     assert e.value.status == 1 and "65535" in str(e.value)
