@@ -496,7 +496,10 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "stage_kernel<float> (fused flux + residual + RK stage)",
-                         "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec], "launch_ms": launch_ms},
+                         "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec], "launch_ms": launch_ms,
+                         "limiter": "instruction issue, not HBM: ncu shows DRAM traffic equal to the algorithmic "
+                                    "bytes at ~25 % of DRAM peak while issue is 65 % active with 16 warps per SM "
+                                    "(124 registers); profiles/stage_kernel_fp32_batch256_ncu.md"},
             "cpu_baseline": None if cpu_v is None else {
                 "value": cpu_all[0], "unit": UNIT, "cores": cpu_all[1], "kind": "oracle",
                 "sample": f"FP64 C oracle as independent processes, one per core, each stepping its share of "
