@@ -182,7 +182,8 @@ roeam_status roeam_edge_rows(roeam_grid *g, int grid_idx, int side, int stage, v
 
 /* Sets the two ghost rows beyond the EXCHANGE side `side` (2 = S: j = -2, -1; 3 = N: j = nj,
  * nj+1) of grid grid_idx, in the state that stage `stage` (0, 1, 2) reads, from src laid out
- * like roeam_edge_rows' output (host or device memory; ordered on the handle's stream). A grid
+ * like roeam_edge_rows' output (host or device memory; ordered on the handle's stream and, for
+ * host memory, complete on return, so the buffer may be reused at once). A grid
  * with an EXCHANGE side keeps these rows in its own state planes; they start at zero, so each
  * must be set before the stage that reads it. */
 roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, const void *src);

@@ -1038,6 +1038,12 @@ roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, co
         CUDA_TRY(cudaMemcpy2DAsync(base + g->esize * (size_t)(k * G.plane), g->esize * G.pitch,
                                    (const char *)src + g->esize * (size_t)(2 * k * G.ni), g->esize * G.ni,
                                    g->esize * G.ni, 2, cudaMemcpyDefault, g->stream));
+    // a host source (page-locked memory copies asynchronously) may be reused once this returns
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, src) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+    }
     return ROEAM_OK;
 }
 
