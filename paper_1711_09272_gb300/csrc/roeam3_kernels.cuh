@@ -227,27 +227,37 @@ template <typename T> __device__ __forceinline__ T min9(T a, T b, T c, T d, T e,
     return vmin(vmin(vmin(a, b), vmin(c, d)), vmin(vmin(e, f), vmin(vmin(g, h), i)));
 }
 
+// Velocity, |q|^2 and pressure of a conserved 3D state, with explicit rounding (the stage
+// epilogue's positivity check and the time-step rate share them).
+template <typename T> struct Prims3 { T ri, u, v, w, q2, p; };
+template <typename T>
+__device__ __forceinline__ Prims3<T> cell_prims3(T r, T ru, T rv, T rw, T rE, const GridCoef3<T> &K)
+{
+    Prims3<T> s;
+    s.ri = rcp(r);
+    s.u = rmul(ru, s.ri); s.v = rmul(rv, s.ri); s.w = rmul(rw, s.ri);
+    s.q2 = radd(radd(rmul(s.u, s.u), rmul(s.v, s.v)), rmul(s.w, s.w));
+    s.p = rmul(K.gm1, rsub(rE, rmul(rmul(T(0.5), r), s.q2)));
+    return s;
+}
+
 // Time-step rate of one 3D cell (the 2D rule with three directions; theta shared).
 template <typename T>
-__device__ __forceinline__ T cell_rate3(T r, T ru, T rv, T rw, T rE, const GridCoef3<T> &K, T &p_out)
+__device__ __forceinline__ T cell_rate3(const Prims3<T> &s, const GridCoef3<T> &K)
 {
-    const T ri = rcp(r);
-    const T u = rmul(ru, ri), v = rmul(rv, ri), w = rmul(rw, ri);
-    const T q2 = radd(radd(rmul(u, u), rmul(v, v)), rmul(w, w));
-    const T p = rmul(K.gm1, rsub(rE, rmul(rmul(T(0.5), r), q2)));
-    p_out = p;
-    const T c2 = rmul(rmul(K.g, p), ri);
+    const T c2 = rmul(rmul(K.g, s.p), s.ri);
     const T c = sqrt0(c2);
-    const T th = vmin(vmax(K.mr2, rmul(q2, rcp(c2))), T(1));
+    const T th = vmin(vmax(K.mr2, rmul(s.q2, rcp(c2))), T(1));
     T wx = c, wy = c, wz = c;
     if (th < T(1)) {
         const T om = rsub(T(1), th), ith = rcp(th);
         const T a = rmul(rmul(T(4), c2), th), o2 = rmul(om, om);
-        wx = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(u, u))))), ith));
-        wy = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(v, v))))), ith));
-        wz = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(w, w))))), ith));
+        wx = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(s.u, s.u))))), ith));
+        wy = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(s.v, s.v))))), ith));
+        wz = vmax(c, rmul(rmul(T(0.5), sqrt0(radd(a, rmul(o2, rmul(s.w, s.w))))), ith));
     }
-    return radd(radd(rmul(radd(vabs(u), wx), K.idx), rmul(radd(vabs(v), wy), K.idy)), rmul(radd(vabs(w), wz), K.idz));
+    return radd(radd(rmul(radd(vabs(s.u), wx), K.idx), rmul(radd(vabs(s.v), wy), K.idy)),
+                rmul(radd(vabs(s.w), wz), K.idz));
 }
 
 // Shared-memory exchange of one plane: fields [9 + NS cell values][3 detector values][NV flux
@@ -428,13 +438,12 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
                     }
 #pragma unroll
                     for (int v = 0; v < NV; ++v) dst[x + v * vol] = out[v];
-                    T p;
-                    const T rt = cell_rate3(out[0], out[1], out[2], out[3], out[4], K, p);
-                    if (!(out[0] > T(0)) || !(p > T(0))) {
-                        const bool fin = isfinite((double)out[0]) && isfinite((double)p);
+                    const Prims3<T> cp = cell_prims3(out[0], out[1], out[2], out[3], out[4], K);
+                    if (!(out[0] > T(0)) || !(cp.p > T(0))) {
+                        const bool fin = isfinite((double)out[0]) && isfinite((double)cp.p);
                         atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
                     } else if (a.want_rate) {
-                        my_rate = vmax(my_rate, rt);
+                        my_rate = vmax(my_rate, cell_rate3(cp, K));
                     }
                 } else {
 #pragma unroll
@@ -478,8 +487,8 @@ __global__ void __launch_bounds__(256) rate3_kernel(const GridDev3 *grids, const
     for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
         const long long i = q % G.ni, jk = q / G.ni;
         const long long c = G.off + jk * G.pitch + i;
-        T p;
-        m = vmax(m, cell_rate3(U[c], U[c + G.vol], U[c + 2 * G.vol], U[c + 3 * G.vol], U[c + 4 * G.vol], K, p));
+        m = vmax(m, cell_rate3(cell_prims3(U[c], U[c + G.vol], U[c + 2 * G.vol], U[c + 3 * G.vol], U[c + 4 * G.vol], K),
+                               K));
     }
     m = block_max<256>(m, red);
     if (threadIdx.x == 0 && m > T(0)) atomicMax(rate + g, rate_bits(m));
