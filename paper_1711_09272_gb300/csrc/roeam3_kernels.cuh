@@ -394,8 +394,13 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
                 const T ay = min9(Py, at(b, NC, ys, lane), at(b, NC, ys, le), Px, Pxe, at(b, NC + 1, ys, lane),
                                   at(b, NC + 2, ys, lane), Pz, Pzt);
                 const T az = min9(Pz, Px_m, Pxe_m, Px, Pxe, Py_m, Pyn_m, Py, Pyn);
-                s1x = detector_of(ax);
-                s1y = detector_of(ay);
+                if constexpr (sizeof(T) == 4) {
+                    const V2 sxy = detector_of(mk2(ax, ay));
+                    s1x = sxy.v.x; s1y = sxy.v.y;
+                } else {
+                    s1x = detector_of(ax);
+                    s1y = detector_of(ay);
+                }
                 s1z = detector_of(az);
             }
 
