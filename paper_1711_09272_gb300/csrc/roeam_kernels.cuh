@@ -818,6 +818,16 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 const int x = j * R.pitch + i;
                 for (int k = 0; k < 4; ++k) Un_next[k] = R.un[x + k * R.plane];
             }
+            // U^(k) of row j-1 for this iteration's epilogue, issued before the faces (the
+            // reconstructing curvilinear kernel, which is latency-bound: +2.4 %; the others
+            // measured slower with it and read it again in the epilogue)
+            T Uk[4] = {T(0), T(0), T(0), T(0)};
+            if constexpr (MUSCL && CURV) {
+                if (stage_mode && out_lane && j > j0) {
+                    const int x = (j - 1) * R.pitch + i;
+                    for (int k = 0; k < 4; ++k) Uk[k] = __ldg(R.src + x + k * R.plane);
+                }
+            }
 
             // ---- the two faces of this lane: west x-face of row j (cells lane-1 | lane) and
             //      the y-face between rows j-1 and j (window H-1 | H)
@@ -954,8 +964,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     if (stage_mode) {
                         T out[4];
                         for (int k = 0; k < 4; ++k) {
-                            // U^(k) of this cell, loaded two iterations ago (an L1 hit)
-                            const T upd = __ldg(R.src + x + k * R.plane) + dt * Rs[k];
+                            // U^(k) of this cell, loaded rows ago (mostly an L1 hit) or above
+                            const T upd = (MUSCL && CURV ? Uk[k] : __ldg(R.src + x + k * R.plane)) + dt * Rs[k];
                             out[k] = combine ? a.alpha * Un[k] + a.beta * upd : upd;
                         }
                         for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = out[k];
