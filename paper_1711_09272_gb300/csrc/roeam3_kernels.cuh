@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
         T acc[NV];
         T Un[NV];
         T my_rate = T(0);
+        T Pz_carry = ratio_P(Wm.r, Wm.p, W0.r, W0.p);   // bottom z-face of plane k0
 
         for (int k = k0; k <= k1; ++k) {
             const int b = k & 1;
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
             // detector values of plane k known to this thread
             const T Px = ratio_P(shup(W0.r, 1), shup(W0.p, 1), W0.r, W0.p);   // west x-face
             const T Pxe = shdn(Px, 1);                                        // east x-face
-            const T Pz = ratio_P(Wm.r, Wm.p, W0.r, W0.p);                     // bottom z-face
+            const T Pz = Pz_carry;                                            // bottom z-face
             const T Pzt = ratio_P(W0.r, W0.p, Wp.r, Wp.p);                    // top z-face
 
             // exchange plane k with the rows above and below
@@ -464,6 +465,7 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
 
             // advance the window
             Px_m = Px; Pxe_m = Pxe; Py_m = Py; Pyn_m = Pyn;
+            Pz_carry = Pzt;   // the top z-face of plane k is the bottom one of plane k + 1
             Wm = W0;
             W0 = Wp;
             finish3<T, NS>(pend, inflow_xy, kx, ky, K, Wp);

@@ -409,7 +409,11 @@ template <typename T> __device__ __forceinline__ T shdn(T v, int d) { return __s
 
 template <typename T> __device__ __forceinline__ T ratio_P(T r0, T p0, T r1, T p1)
 {
-    return vmin(vmin(p0, p1) / vmax(p0, p1), vmin(r0, r1) / vmax(r0, r1));   // Eq. 97
+    // Eq. 97; in FP32 each ratio is the smaller value times the reciprocal of the larger
+    if constexpr (sizeof(T) == 4)
+        return vmin(vmin(p0, p1) * rcp(vmax(p0, p1)), vmin(r0, r1) * rcp(vmax(r0, r1)));
+    else
+        return vmin(vmin(p0, p1) / vmax(p0, p1), vmin(r0, r1) / vmax(r0, r1));
 }
 
 // MUSCL limited slope: minmod(a, b) = (sgn a + sgn b)/2 min(|a|, |b|); van Leer
