@@ -973,13 +973,20 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                             out[k] = combine ? a.alpha * Un[k] + a.beta * upd : upd;
                         }
                         for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = out[k];
-                        if (!solid) {
+                        if (!solid && a.want_rate) {
                             const CellPrims<T> cp = cell_prims(out[0], out[1], out[2], out[3], K);
                             if (!(out[0] > T(0)) || !(cp.p > T(0))) {
                                 const bool fin = isfinite((double)out[0]) && isfinite((double)cp.p);
                                 atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
-                            } else if (a.want_rate) {
+                            } else {
                                 my_rate = vmax(my_rate, cell_rate<CURV>(cp, cg, K));
+                            }
+                        } else if (!solid) {
+                            // p > 0 without the division: 2 rho (rho E) > (rho u)^2 + (rho v)^2
+                            const T e2 = T(2) * out[0] * out[3], m2 = out[1] * out[1] + out[2] * out[2];
+                            if (!(out[0] > T(0)) || !(e2 > m2)) {
+                                const bool fin = isfinite((double)out[0]) && isfinite((double)(e2 - m2));
+                                atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
                             }
                         }
                     } else if (a.mode == MODE_RESIDUAL) {
