@@ -444,12 +444,22 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
                     }
 #pragma unroll
                     for (int v = 0; v < NV; ++v) dst[x + v * vol] = out[v];
-                    const Prims3<T> cp = cell_prims3(out[0], out[1], out[2], out[3], out[4], K);
-                    if (!(out[0] > T(0)) || !(cp.p > T(0))) {
-                        const bool fin = isfinite((double)out[0]) && isfinite((double)cp.p);
-                        atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
-                    } else if (a.want_rate) {
-                        my_rate = vmax(my_rate, cell_rate3(cp, K));
+                    if (a.want_rate) {
+                        const Prims3<T> cp = cell_prims3(out[0], out[1], out[2], out[3], out[4], K);
+                        if (!(out[0] > T(0)) || !(cp.p > T(0))) {
+                            const bool fin = isfinite((double)out[0]) && isfinite((double)cp.p);
+                            atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
+                        } else {
+                            my_rate = vmax(my_rate, cell_rate3(cp, K));
+                        }
+                    } else {
+                        // p > 0 without the division: 2 rho (rho E) > |rho q|^2
+                        const T e2 = T(2) * out[0] * out[4];
+                        const T m2 = out[1] * out[1] + out[2] * out[2] + out[3] * out[3];
+                        if (!(out[0] > T(0)) || !(e2 > m2)) {
+                            const bool fin = isfinite((double)out[0]) && isfinite((double)(e2 - m2));
+                            atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
+                        }
                     }
                 } else {
 #pragma unroll
