@@ -453,12 +453,16 @@ __global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1
                             my_rate = vmax(my_rate, cell_rate3(cp, K));
                         }
                     } else {
-                        // p > 0 without the division: 2 rho (rho E) > |rho q|^2
+                        // p > 0 without the division: 2 rho (rho E) > |rho q|^2; a cell that fails
+                        // it (rare: also products beyond the FP32 range) is decided by its pressure
                         const T e2 = T(2) * out[0] * out[4];
                         const T m2 = out[1] * out[1] + out[2] * out[2] + out[3] * out[3];
                         if (!(out[0] > T(0)) || !(e2 > m2)) {
-                            const bool fin = isfinite((double)out[0]) && isfinite((double)(e2 - m2));
-                            atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
+                            const Prims3<T> cp = cell_prims3(out[0], out[1], out[2], out[3], out[4], K);
+                            if (!(out[0] > T(0)) || !(cp.p > T(0))) {
+                                const bool fin = isfinite((double)out[0]) && isfinite((double)cp.p);
+                                atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
+                            }
                         }
                     }
                 } else {

@@ -417,16 +417,18 @@ template <typename T> __device__ __forceinline__ T ratio_P(T r0, T p0, T r1, T p
 }
 
 // MUSCL limited slope: minmod(a, b) = (sgn a + sgn b)/2 min(|a|, |b|); van Leer
-// (a|b| + |a|b) / (|a| + |b|), 0 when ab <= 0.
+// (a|b| + |a|b) / (|a|+|b|) = 2 a |b| / (|a| + |b|), 0 when ab <= 0. The sign test and the van
+// Leer quotient avoid the product a b, which in FP32 underflows for differences below ~1e-19
+// (a state scaled by 1e-24 is as valid as the unscaled one).
 template <typename V> __device__ __forceinline__ V limiter(bool vanleer, V a, V b)
 {
     const V zero = splat<V>(0);
+    const auto keep = gt(a * vcopysign(splat<V>(1), b), zero);   // same signs, a != 0
     if (vanleer) {
-        const auto keep = gt(a * b, zero);
         const V aa = vabs(a), ab = vabs(b);
-        return sel(keep, vfma(a, ab, aa * b) * rcp(sel(keep, aa + ab, splat<V>(1))), zero);
+        return sel(keep, (a + a) * (ab * rcp(aa + ab)), zero);
     }
-    return sel(gt(a * b, zero), sel(gt(a, zero), vmin(a, b), vmax(a, b)), zero);
+    return sel(keep, sel(gt(a, zero), vmin(a, b), vmax(a, b)), zero);
 }
 
 // Cell-window entry: primitives (rho, u, v, p) in the global frame, the derived face
@@ -982,11 +984,16 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                                 my_rate = vmax(my_rate, cell_rate<CURV>(cp, cg, K));
                             }
                         } else if (!solid) {
-                            // p > 0 without the division: 2 rho (rho E) > (rho u)^2 + (rho v)^2
+                            // p > 0 without the division: 2 rho (rho E) > (rho u)^2 + (rho v)^2; a cell
+                            // that fails it (rare: also products beyond the FP32 range) is decided
+                            // by its pressure
                             const T e2 = T(2) * out[0] * out[3], m2 = out[1] * out[1] + out[2] * out[2];
                             if (!(out[0] > T(0)) || !(e2 > m2)) {
-                                const bool fin = isfinite((double)out[0]) && isfinite((double)(e2 - m2));
-                                atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
+                                const CellPrims<T> cp = cell_prims(out[0], out[1], out[2], out[3], K);
+                                if (!(out[0] > T(0)) || !(cp.p > T(0))) {
+                                    const bool fin = isfinite((double)out[0]) && isfinite((double)cp.p);
+                                    atomicOr(a.status, fin ? ST_NONPOSITIVE : ST_NONFINITE);
+                                }
                             }
                         }
                     } else if (a.mode == MODE_RESIDUAL) {

@@ -341,3 +341,13 @@ def test_largest_batch_count():
     for k in list(range(0, 65535, 1000)) + [65534]:
         Uo, _ = oracle.OracleGrid(specs[k]).step(U0[k], dt_fixed=float(dts[k]))
         assert rel_state_err(U1[k], Uo) <= TOL[32], k
+
+
+@pytest.mark.parametrize("recon", [0, 2])
+def test_tiny_magnitudes(recon):
+    """The Euler equations are invariant under rho -> s rho, p -> s p at fixed velocity: a state
+    scaled by s = 1e-24 (products of two conserved values then fall below the FP32 range) must
+    step in FP32 without a positivity report and match the oracle."""
+    spec = W.GridSpec(ni=40, nj=24, dx=0.02, dy=0.02, params=W.SchemeParams(m_ref=0.5, recon=recon))
+    U = W.random_smooth_state(spec, seed=5, mach=0.5, amp=0.2) * 1e-24
+    assert one_step_parity(spec, U, 32) <= TOL[32]
