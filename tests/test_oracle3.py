@@ -248,3 +248,21 @@ def test_long_double_bound():
     R = g.residual(U)
     Rl = g.residual(U, long_double=True)
     assert np.max(np.abs(R - Rl)) <= 1e-13 * np.max(np.abs(Rl))
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_power_of_two_density_pressure_scaling_is_exact_3d(walls):
+    """rho -> s rho, p -> s p (scalars k unchanged, so rho k -> s rho k) at fixed velocity
+    leaves the equations unchanged; with s = 2^-60 the 3D oracle's step of the scaled state is
+    the scaled step bit for bit, with the same dt (no additive floor or threshold on rho or p)."""
+    s = 2.0 ** -60
+    bc = (W.INFLOW, W.OUTFLOW, W.WALL, W.WALL, W.WALL, W.OUTFLOW) if walls else (W.PERIODIC,) * 6
+    params = W.SchemeParams(m_ref=0.3, eps1=1)
+    kw = dict(ni=9, nj=8, nk=7, dx=0.05, dy=0.04, dz=0.06, nscal=1, bc=bc, params=params)
+    base = W.GridSpec3(inflow=(1.2, 0.6, 0.1, -0.05, 0.9, 0.3), **kw)
+    scaled = W.GridSpec3(inflow=(1.2 * s, 0.6, 0.1, -0.05, 0.9 * s, 0.3), **kw)
+    U = W.random_rough_state3(base, seed=19, mach=0.9)
+    U1, dt1 = oracle.OracleGrid3(base).step(U, cfl=0.4, nsteps=2)
+    U2, dt2 = oracle.OracleGrid3(scaled).step(U * s, cfl=0.4, nsteps=2)
+    assert dt1 == dt2
+    assert np.array_equal(U2, U1 * s)
