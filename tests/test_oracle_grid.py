@@ -386,3 +386,20 @@ def test_power_of_two_density_pressure_scaling_is_exact(recon, walls):
     U2, dt2 = oracle.OracleGrid(scaled).step(U * s, cfl=0.4, nsteps=2)
     assert dt1 == dt2
     assert np.array_equal(U2, U1 * s)
+
+
+@pytest.mark.parametrize("recon", [0, 2])
+def test_periodic_shift_invariance_is_exact(recon):
+    """On a fully periodic grid no cell is special: stepping a state shifted by (3, 5) cells
+    gives the shifted step, with the same dt, up to rounding (the oracle builds face vectors
+    and volumes from vertex coordinates, whose differences round differently from cell to
+    cell); a wrong index in the periodic wrap of the faces, the detector's transverse faces or
+    the reconstruction stencil changes cells near the seam at first order."""
+    spec = W.GridSpec(ni=19, nj=14, dx=0.05, dy=0.04, params=W.SchemeParams(m_ref=0.3, recon=recon, eps1=1))
+    U = W.random_rough_state(spec, seed=23, mach=0.9, jump=0.5)
+    U1, dt1 = oracle.OracleGrid(spec).step(U, cfl=0.4, nsteps=2)
+    Us = np.roll(U, (5, 3), axis=(1, 2))
+    U2, dt2 = oracle.OracleGrid(spec).step(Us, cfl=0.4, nsteps=2)
+    assert abs(dt2 - dt1) <= 1e-13 * dt1
+    err = np.abs(U2 - np.roll(U1, (5, 3), axis=(1, 2))).reshape(4, -1).max(axis=1)
+    assert np.all(err <= 1e-13 * np.abs(U1).reshape(4, -1).max(axis=1)), err
