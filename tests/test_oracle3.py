@@ -278,3 +278,24 @@ def test_periodic_shift_invariance_is_exact_3d():
     U2, dt2 = oracle.OracleGrid3(spec).step(Us, cfl=0.4, nsteps=2)
     assert dt1 == dt2
     assert np.array_equal(U2, np.roll(U1, (4, 3, 2), axis=(1, 2, 3)))
+
+
+@pytest.mark.parametrize("eps1", [0, 1])
+def test_stationary_contact_and_shear_layer_are_exact_3d(eps1):
+    """The 3D forms of two exact steady solutions: a stationary contact (rho and the scalar
+    varying from cell to cell, zero velocity, p uniform) and a shear layer (w varying with x
+    only, tangential to the x-faces across which it jumps; u = v = 0; rho, p, k uniform).
+    Every dissipation term vanishes at zero normal velocity without normal-velocity or pressure
+    jumps, and the rotated-Riemann estimate is |U^| = 0: the residual is exactly zero."""
+    rng = W.SplitMix64(37)
+    spec = W.GridSpec3(ni=9, nj=8, nk=7, dx=0.05, dy=0.04, dz=0.06, nscal=1, params=W.SchemeParams(m_ref=0.3, eps1=eps1))
+    g = spec.params.gamma
+    shape = (spec.nk, spec.nj, spec.ni)
+    rho = 0.3 + 2.0 * rng.uniforms(int(np.prod(shape))).reshape(shape)
+    k = rng.uniforms(int(np.prod(shape))).reshape(shape)
+    zero = np.zeros(shape)
+    contact = np.stack([rho, zero, zero, zero, np.full(shape, 1.0 / (g - 1)), rho * k])
+    w = np.broadcast_to(rng.uniforms(spec.ni)[None, None, :] - 0.5, shape)
+    shear = np.stack([np.ones(shape), zero, zero, w, 1.0 / (g - 1) + 0.5 * w * w, np.full(shape, 0.4)])
+    for U in (contact, shear):
+        assert np.all(oracle.OracleGrid3(spec).residual(U) == 0.0)

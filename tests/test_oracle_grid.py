@@ -403,3 +403,25 @@ def test_periodic_shift_invariance_is_exact(recon):
     assert abs(dt2 - dt1) <= 1e-13 * dt1
     err = np.abs(U2 - np.roll(U1, (5, 3), axis=(1, 2))).reshape(4, -1).max(axis=1)
     assert np.all(err <= 1e-13 * np.abs(U1).reshape(4, -1).max(axis=1)), err
+
+
+@pytest.mark.parametrize("recon", [0, 1, 2])
+@pytest.mark.parametrize("eps1", [0, 1])
+def test_stationary_contact_and_shear_layer_are_exact(recon, eps1):
+    """Two exact steady solutions that a Roe-type dissipation must leave alone: a stationary
+    contact (rho varying from cell to cell, u = v = 0, p uniform) and a stationary shear layer
+    (v varying with x only, u = 0, rho and p uniform). On every face the normal velocity and
+    the jumps of normal velocity and pressure are zero, so each term of Eq. 85's dissipation
+    vanishes (xi of Eq. 86 and its eps1 floor, dp_p, dp_u, dU_p, dU_u; for the shear layer the
+    rotated-Riemann estimate of Eqs. 103-109 is |U^| = 0), and the central fluxes of a cell's
+    opposite faces cancel: the residual is exactly zero."""
+    rng = W.SplitMix64(31)
+    spec = W.GridSpec(ni=16, nj=12, dx=0.05, dy=0.04, params=W.SchemeParams(m_ref=0.3, recon=recon, eps1=eps1))
+    g = spec.params.gamma
+    rho = 0.3 + 2.0 * rng.uniforms(spec.ni * spec.nj).reshape(spec.nj, spec.ni)
+    zero = np.zeros_like(rho)
+    contact = np.stack([rho, zero, zero, np.full_like(rho, 1.0 / (g - 1))])
+    v = np.broadcast_to(rng.uniforms(spec.ni)[None, :] - 0.5, rho.shape)
+    shear = np.stack([np.ones_like(rho), zero, v, 1.0 / (g - 1) + 0.5 * v * v])
+    for U in (contact, shear):
+        assert np.all(oracle.OracleGrid(spec).residual(U) == 0.0)
