@@ -88,6 +88,8 @@ def _lib(long_double: bool = False):
             getattr(lib, "orc_rk_step" + sfx).argtypes = [C.POINTER(OrcGrid), dp, C.c_double, C.c_double]
             getattr(lib, "orc_totals" + sfx).argtypes = [C.POINTER(OrcGrid), dp, dp]
             getattr(lib, "orc_detector" + sfx).argtypes = [C.POINTER(OrcGrid), dp, dp, dp]
+            ip = C.POINTER(C.c_int)
+            getattr(lib, "orc_face_states" + sfx).argtypes = [C.POINTER(OrcGrid), dp, C.c_int, ip, ip, dp, dp]
             getattr(lib, "orc3_face_flux" + sfx).argtypes = [C.POINTER(Orc3Params), C.c_int, dp, dp, dp, dp, dp]
             getattr(lib, "orc3_residual" + sfx).argtypes = [C.POINTER(Orc3Grid), dp, dp]
             getattr(lib, "orc3_max_rate" + sfx).restype = C.c_double
@@ -176,6 +178,19 @@ class OracleGrid:
         out = np.zeros(4)
         _fn("orc_totals")(C.byref(self.g), _dptr(U), _dptr(out))
         return out
+
+    def face_states(self, U, cells, dirs) -> Tuple[np.ndarray, np.ndarray]:
+        """Reconstructed left / right primitives (rho, u, v, p) of the faces between cell
+        cells[f] = (i, j) and its +i (dirs[f] = 0) or +j (dirs[f] = 1) neighbour: (n, 4) each."""
+        U = self._u(U)
+        ij = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 2))
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dirs, dtype=np.int32), (ij.shape[0],)))
+        WL = np.zeros((ij.shape[0], 4))
+        WR = np.zeros((ij.shape[0], 4))
+        ip = C.POINTER(C.c_int)
+        _fn("orc_face_states")(C.byref(self.g), _dptr(U), ij.shape[0], ij.ctypes.data_as(ip), d.ctypes.data_as(ip),
+                               _dptr(WL), _dptr(WR))
+        return WL, WR
 
     def detector(self, U) -> Tuple[np.ndarray, np.ndarray]:
         U = self._u(U)

@@ -412,60 +412,70 @@ static real limiter(int kind, real a, real b)
     return (a * RABS_(b) + RABS_(a) * b) / (RABS_(a) + RABS_(b));
 }
 
-/* Flux F*|S| through the face between cells A = (i, j) and B = (i+di, j+dj), (di, dj) in
- * {(1,0), (0,1)}, with face vector S pointing from A to B. Returns 0 and F = 0 when both
- * sides are solid. */
-static int face_flux_grid(const field *fd, int i, int j, int di, int dj, real Sx, real Sy, real F[4])
+/* Left and right states of the face between cells A = (i, j) and B = (i+di, j+dj), (di, dj)
+ * in {(1,0), (0,1)}, with unit normal (nx, ny) from A to B. A wall face (a solid or WALL-ghost
+ * side) takes the first-order fluid state and its mirror image about the face; otherwise the
+ * cell states, reconstructed by MUSCL when recon != 0. Returns 0 when both sides are solid
+ * (no face), else 1. */
+static int face_states(const field *fd, int i, int j, int di, int dj, real nx, real ny, real WL[4], real WR[4])
 {
     const orc_grid *g = fd->g;
     real A[4], B[4];
     int sA, wA, sB, wB;
     ext_state(fd, i, j, A, &sA, &wA);
     ext_state(fd, i + di, j + dj, B, &sB, &wB);
-    real len = RSQRT_(Sx * Sx + Sy * Sy);
-    real nx = Sx / len, ny = Sy / len;
-    for (int k = 0; k < 4; ++k) F[k] = 0;
     if (sA && sB) return 0;
-
-    real WL[4], WR[4];
     if (sA || sB || wA || wB) {
         /* Wall face: first-order fluid state and its mirror image about this face. */
         if (sA || wA) { memcpy(WR, B, sizeof(B)); mirror(B, nx, ny, WL); }
         else { memcpy(WL, A, sizeof(A)); mirror(A, nx, ny, WR); }
-    } else {
-        memcpy(WL, A, sizeof(A));
-        memcpy(WR, B, sizeof(B));
-        if (g->prm.recon) {
-            real Am[4], Bp[4];
-            int s, w;
-            ext_state(fd, i - di, j - dj, Am, &s, &w);
-            if (s) {   /* stencil cell is solid: mirror of A about the face between them */
-                real tx, ty;
-                if (di) xface_S(g, i, j, &tx, &ty); else yface_S(g, i, j, &tx, &ty);
-                real l = RSQRT_(tx * tx + ty * ty);
-                mirror(A, tx / l, ty / l, Am);
-            }
-            ext_state(fd, i + 2 * di, j + 2 * dj, Bp, &s, &w);
-            if (s) {
-                real tx, ty;
-                if (di) xface_S(g, i + 2, j, &tx, &ty); else yface_S(g, i, j + 2, &tx, &ty);
-                real l = RSQRT_(tx * tx + ty * ty);
-                mirror(B, tx / l, ty / l, Bp);
-            }
-            real rL[4], rR[4];
-            for (int k = 0; k < 4; ++k) {
-                rL[k] = A[k] + (real)0.5 * limiter(g->prm.recon, A[k] - Am[k], B[k] - A[k]);
-                rR[k] = B[k] - (real)0.5 * limiter(g->prm.recon, B[k] - A[k], Bp[k] - B[k]);
-            }
-            /* Positivity of the reconstructed density and pressure, else first order. */
-            if (rL[0] > 0 && rL[3] > 0 && rR[0] > 0 && rR[3] > 0) {
-                memcpy(WL, rL, sizeof(rL));
-                memcpy(WR, rR, sizeof(rR));
-            }
+        return 1;
+    }
+    memcpy(WL, A, sizeof(A));
+    memcpy(WR, B, sizeof(B));
+    if (g->prm.recon) {
+        real Am[4], Bp[4];
+        int s, w;
+        ext_state(fd, i - di, j - dj, Am, &s, &w);
+        if (s) {   /* stencil cell is solid: mirror of A about the face between them */
+            real tx, ty;
+            if (di) xface_S(g, i, j, &tx, &ty); else yface_S(g, i, j, &tx, &ty);
+            real l = RSQRT_(tx * tx + ty * ty);
+            mirror(A, tx / l, ty / l, Am);
+        }
+        ext_state(fd, i + 2 * di, j + 2 * dj, Bp, &s, &w);
+        if (s) {
+            real tx, ty;
+            if (di) xface_S(g, i + 2, j, &tx, &ty); else yface_S(g, i, j + 2, &tx, &ty);
+            real l = RSQRT_(tx * tx + ty * ty);
+            mirror(B, tx / l, ty / l, Bp);
+        }
+        real rL[4], rR[4];
+        for (int k = 0; k < 4; ++k) {
+            rL[k] = A[k] + (real)0.5 * limiter(g->prm.recon, A[k] - Am[k], B[k] - A[k]);
+            rR[k] = B[k] - (real)0.5 * limiter(g->prm.recon, B[k] - A[k], Bp[k] - B[k]);
+        }
+        /* Positivity of the reconstructed density and pressure, else first order. */
+        if (rL[0] > 0 && rL[3] > 0 && rR[0] > 0 && rR[3] > 0) {
+            memcpy(WL, rL, sizeof(rL));
+            memcpy(WR, rR, sizeof(rR));
         }
     }
+    return 1;
+}
+
+/* Flux F*|S| through the face between cells A = (i, j) and B = (i+di, j+dj), (di, dj) in
+ * {(1,0), (0,1)}, with face vector S pointing from A to B. Returns 0 and F = 0 when both
+ * sides are solid. */
+static int face_flux_grid(const field *fd, int i, int j, int di, int dj, real Sx, real Sy, real F[4])
+{
+    real len = RSQRT_(Sx * Sx + Sy * Sy);
+    real nx = Sx / len, ny = Sy / len;
+    real WL[4], WR[4];
+    for (int k = 0; k < 4; ++k) F[k] = 0;
+    if (!face_states(fd, i, j, di, dj, nx, ny, WL, WR)) return 0;
     real s1 = detector_s1(fd, i, j, di, dj);
-    face_flux(&g->prm, WL, WR, nx, ny, s1, F);
+    face_flux(&fd->g->prm, WL, WR, nx, ny, s1, F);
     for (int k = 0; k < 4; ++k) F[k] *= len;
     return 1;
 }
@@ -639,5 +649,27 @@ void ORC_API(orc_detector)(const orc_grid *g, const double *U, double *sx, doubl
     for (int jc = 0; jc <= g->nj; ++jc)
         for (int i = 0; i < g->ni; ++i)
             sy[(size_t)jc * g->ni + i] = (double)detector_s1(&fd, i, jc - 1, 0, 1);
+    free(W);
+}
+
+/* Left and right primitive states (rho, u, v, p) of n faces, for tests: face f lies between
+ * cell (ij[2f], ij[2f+1]) and its neighbour in +i (dir[f] = 0) or +j (dir[f] = 1); WL and WR
+ * receive 4 values per face. A face with two solid sides gives zeros. */
+void ORC_API(orc_face_states)(const orc_grid *g, const double *U, int n, const int *ij, const int *dir, double *WL,
+                              double *WR)
+{
+    const size_t N = (size_t)g->ni * g->nj;
+    real *W = (real *)malloc(4 * N * sizeof(real));
+    field fd = {g, W};
+    to_prim(g, U, W);
+    for (int f = 0; f < n; ++f) {
+        const int i = ij[2 * f], j = ij[2 * f + 1], di = dir[f] ? 0 : 1, dj = dir[f] ? 1 : 0;
+        real Sx, Sy;
+        if (di) xface_S(g, i + 1, j, &Sx, &Sy); else yface_S(g, i, j + 1, &Sx, &Sy);
+        real len = RSQRT_(Sx * Sx + Sy * Sy);
+        real L[4] = {0, 0, 0, 0}, R[4] = {0, 0, 0, 0};
+        face_states(&fd, i, j, di, dj, Sx / len, Sy / len, L, R);
+        for (int k = 0; k < 4; ++k) { WL[4 * f + k] = (double)L[k]; WR[4 * f + k] = (double)R[k]; }
+    }
     free(W);
 }
