@@ -477,6 +477,26 @@ def run_ours(args):
                "path": "roeam_step_host(pinned fp64 in, pinned fp64 out, 1 step): chunked, copies overlapped",
                "separate_calls": {"value": total_cells * 3 / sep_s / 1e9,
                                   "path": "roeam_set_state + roeam_rk_step(1) + roeam_get_state (pinned fp64)"}}
+        # a caller whose float64 state already lives on the GPU (device-pointer state I/O)
+        d_in = h_in.to("cuda")
+        d_out = torch.empty_like(d_in)
+        b.set_state_device(d_in, -1, stream=stream.cuda_stream)
+        b.step(cfl=0.5, nsteps=1)
+        b.get_state_device(d_out, -1, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        ed0, ed1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ed0.record(stream)
+        for _ in range(e2e_steps):
+            b.set_state_device(d_in, -1, stream=stream.cuda_stream)
+            b.step(cfl=0.5, nsteps=1)
+            b.get_state_device(d_out, -1, stream=stream.cuda_stream)
+        ed1.record(stream)
+        torch.cuda.synchronize()
+        dev_ms = reduce_max(ed0.elapsed_time(ed1) / e2e_steps, world)
+        e2e["device_resident_fp64"] = {
+            "value": total_cells * 3 / (dev_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": dev_ms,
+            "path": "roeam_set_state_device + roeam_rk_step(1) + roeam_get_state_device (float64 CUDA tensors)"}
+        del d_in, d_out
 
     line = None
     if rank == 0:
@@ -499,7 +519,7 @@ def run_ours(args):
                          "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec], "launch_ms": launch_ms,
                          "limiter": "instruction issue, not HBM: ncu shows DRAM traffic equal to the algorithmic "
                                     "bytes at ~25 % of DRAM peak while issue is 65 % active with 16 warps per SM "
-                                    "(124 registers); profiles/stage_kernel_fp32_batch256_ncu.md"},
+                                    "(124 registers); see the ncu summary of this kernel"},
             "cpu_baseline": None if cpu_v is None else {
                 "value": cpu_all[0], "unit": UNIT, "cores": cpu_all[1], "kind": "oracle",
                 "sample": f"FP64 C oracle as independent processes, one per core, each stepping its share of "

@@ -139,6 +139,21 @@ roeam_status roeam_set_state(roeam_grid *g, int grid_idx, const double *cons);
  * Synchronises; reports pending device errors. */
 roeam_status roeam_get_state(roeam_grid *g, int grid_idx, double *cons_out);
 
+/* Device-pointer forms of roeam_set_state / roeam_get_state, for callers whose state already
+ * lives on the GPU (a PyTorch tensor, another solver's buffer): the paper has no counterpart;
+ * the survey of this library's interface lists them as the optional device variants of the
+ * state calls. cons_dev / cons_out_dev is float64 device memory of the handle's device (or
+ * managed memory), 8-byte aligned, laid out like the host arrays ([4][nj][ni] per grid, grids
+ * concatenated for grid_idx = -1); the caller owns it. cuda_stream (a cudaStream_t, or NULL
+ * for the legacy default stream) orders the call with the caller's work: what the caller
+ * submitted to it before the call completes before the library reads (set) or writes (get)
+ * the array, and what the caller submits to it afterwards runs after the library has
+ * finished with the array. The host does not wait; device errors of earlier steps are
+ * reported by the next synchronising call. Wrong pointers (host memory, another device,
+ * misaligned) give ROEAM_E_ARG. set refreshes the time-step estimate like roeam_set_state. */
+roeam_status roeam_set_state_device(roeam_grid *g, int grid_idx, const double *cons_dev, void *cuda_stream);
+roeam_status roeam_get_state_device(roeam_grid *g, int grid_idx, double *cons_out_dev, void *cuda_stream);
+
 /* Evaluates the finite-volume residual R(U) = -(1/V) sum_f F_f |S_f| (outward faces,
  * Roe-AM flux of Eqs. 85-109) of grid `grid_idx` (or all) for the current state and
  * copies it to res_out (same layout as the state; solid cells get 0). res_out may be
@@ -218,9 +233,12 @@ roeam_status roeam_check(roeam_grid *g);
  * 24 MiB array that every GPU loading the library holds until the process exits. A grid
  * fits if 4 x nj x pitch working-precision values (pitch = ni rounded up to 32) plus
  * 4 x ni x nj doubles fit in it (about 512 x 512 cells); larger grids get ROEAM_E_ARG with
- * a message saying so. The first call on a device looks the array up (once per device);
- * make that first call before any stream capture. Calls share the array: calls whose work
- * overlaps on the GPU race. Synchronises. */
+ * a message saying so. The array is committed on a device when the first handle on that
+ * device is created (roeam_create_grid looks it up there, which makes CUDA load the module
+ * holding it), so a caller that creates its handles at start-up has the array before it
+ * stops allocating, and this call itself allocates nothing. Calls share the array and it
+ * keeps the last call's contents (each call writes all it reads); calls whose work overlaps
+ * on the GPU race. Synchronises. */
 roeam_status roeam_flux_residual_noalloc(roeam_grid *g, int grid_idx, double *res_out);
 
 /* Number of tile shapes (stage-kernel variants) the library is built with. */

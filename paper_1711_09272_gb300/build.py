@@ -21,6 +21,10 @@ SOURCES = ["roeam_api.cu", "roeam_k32.cu", "roeam_k64.cu", "roeam_k32_abl.cu", "
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--prec-div=false", "--prec-sqrt=false",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+# The 2D translation units write every fused multiply-add out explicitly and forbid the
+# compiler from forming others, so that results are bit-identical across work-unit layouts
+# (tile shapes, row slabs) and across the copies of an unrolled loop body.
+EXACT_FMA = {"roeam_api.cu", "roeam_k32.cu", "roeam_k64.cu", "roeam_k32_abl.cu", "roeam_k64_abl.cu"}
 
 
 def nvcc() -> str:
@@ -48,7 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(OUT_DIR, os.path.splitext(s)[0] + ".o") for s in SOURCES]
 
     def compile_one(k):
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, SOURCES[k]), "-o", objs[k]]
+        extra = ["-fmad=false"] if SOURCES[k] in EXACT_FMA else []
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, SOURCES[k]), "-o", objs[k]]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -92,6 +92,7 @@ struct roeam_grid {
     double *h_red = nullptr;                             // pinned 8 doubles
     unsigned long long *h_rate = nullptr;                // pinned count
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;     // ordering against a caller's stream (device-pointer I/O)
     long long step = 0;
     unsigned long long launches = 0;
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -301,7 +302,9 @@ roeam_status rk_steps(roeam_grid *g, double cfl, double dt_fixed, int nsteps)
             for (int s = 0; s < GRAPH_STEPS; ++s) {
                 roeam_status st = launch_step<T>(g, g->cap_stream, s, cfl, dt_fixed);
                 if (st != ROEAM_OK) {
+                    graph = nullptr;
                     cudaStreamEndCapture(g->cap_stream, &graph);
+                    if (graph) cudaGraphDestroy(graph);
                     return st;
                 }
             }
@@ -374,6 +377,51 @@ roeam_status do_get(roeam_grid *g, int idx, const void *src, double *out)
     CUDA_TRY(cudaMemcpyAsync(out, g->staging + p0, sizeof(double) * (p1 - p0), cudaMemcpyDeviceToHost, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     return ROEAM_OK;
+}
+
+// Device-pointer state I/O: the caller's float64 array lives on the handle's device. Work
+// already submitted to the caller's stream `cs` is finished before the library reads or
+// writes the array, and work submitted to `cs` afterwards waits for the library's kernels;
+// the host does not wait. (cs equal to the handle's stream needs neither.)
+roeam_status order_after(roeam_grid *g, cudaStream_t cs)
+{
+    if (cs == g->stream) return ROEAM_OK;
+    CUDA_TRY(cudaEventRecord(g->ev_in, cs));
+    CUDA_TRY(cudaStreamWaitEvent(g->stream, g->ev_in, 0));
+    return ROEAM_OK;
+}
+roeam_status order_before(roeam_grid *g, cudaStream_t cs)
+{
+    if (cs == g->stream) return ROEAM_OK;
+    CUDA_TRY(cudaEventRecord(g->ev_out, g->stream));
+    CUDA_TRY(cudaStreamWaitEvent(cs, g->ev_out, 0));
+    return ROEAM_OK;
+}
+
+template <typename T>
+roeam_status do_set_state_device(roeam_grid *g, int idx, const double *cons, cudaStream_t cs)
+{
+    const int lo = idx < 0 ? 0 : idx, hi = idx < 0 ? g->count : idx + 1;
+    roeam_status st = order_after(g, cs);
+    if (st != ROEAM_OK) return st;
+    CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, cons, (T *)g->U, g->stream, g->hg[lo].poff));
+    g->launches += 1;
+    st = refresh_rate<T>(g, lo, hi);
+    if (st != ROEAM_OK) return st;
+    for (int k = lo; k < hi; ++k) g->state_set[k] = 1;
+    return order_before(g, cs);
+}
+
+template <typename T>
+roeam_status do_get_state_device(roeam_grid *g, int idx, double *out, cudaStream_t cs)
+{
+    const int lo = idx < 0 ? 0 : idx, hi = idx < 0 ? g->count : idx + 1;
+    roeam_status st = order_after(g, cs);
+    if (st != ROEAM_OK) return st;
+    CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)g->U, out, g->stream, 0,
+                                  g->hg[lo].poff));
+    g->launches += 1;
+    return order_before(g, cs);
 }
 
 template <typename T>
@@ -527,6 +575,11 @@ roeam_status do_stage(roeam_grid *g, int stage, double dt)
 
 // The state buffer that stage `stage` reads: U^n, U1 or U2.
 void *stage_source(roeam_grid *g, int stage) { return stage == 0 ? g->U : (stage == 1 ? g->A : g->B); }
+
+// Device address of the allocation-free residual's scratch array (defined at the end of this
+// file); roeam_create_grid looks it up so that the array is committed on the device when a
+// handle is made.
+roeam_status noalloc_scratch(int device, void **out);
 
 }  // namespace
 
@@ -699,6 +752,8 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
 
     CREATE_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     CREATE_TRY(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));
+    CREATE_TRY(cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming));
+    CREATE_TRY(cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming));
     CREATE_TRY(cudaMalloc(&g->d_grids, sizeof(GridDev) * count));
     const size_t sbytes = g->esize * (size_t)g->total_elems;
     CREATE_TRY(cudaMalloc(&g->U, sbytes));
@@ -736,6 +791,12 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
     if (st != ROEAM_OK) return cleanup(st);
     st = setup_tiles(g, 0);
     if (st != ROEAM_OK) return cleanup(st);
+    // Load the module that holds the allocation-free residual's scratch array now (CUDA loads
+    // modules lazily, and committing the array is an allocation), so that a caller which makes
+    // its handles at start-up has the array before it stops allocating.
+    void *scratch = nullptr;
+    st = noalloc_scratch(device, &scratch);
+    if (st != ROEAM_OK) return cleanup(st);
 #undef CREATE_TRY
     *out = g;
     return ROEAM_OK;
@@ -765,6 +826,8 @@ void roeam_destroy_grid(roeam_grid *g)
     if (g->h_red) cudaFreeHost(g->h_red);
     if (g->h_rate) cudaFreeHost(g->h_rate);
     if (g->ev) cudaEventDestroy(g->ev);
+    if (g->ev_in) cudaEventDestroy(g->ev_in);
+    if (g->ev_out) cudaEventDestroy(g->ev_out);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     for (int k = 0; k < 3; ++k)
         if (g->pipe[k]) cudaStreamDestroy(g->pipe[k]);
@@ -779,6 +842,46 @@ roeam_status roeam_set_state(roeam_grid *g, int grid_idx, const double *cons)
     if (!cons) return fail(ROEAM_E_ARG, "cons must be non-null");
     CUDA_TRY(cudaSetDevice(g->device));
     return g->precision == 32 ? do_set_state<float>(g, grid_idx, cons) : do_set_state<double>(g, grid_idx, cons);
+}
+
+// A device pointer of the handle's device (or managed memory), else ROEAM_E_ARG.
+static roeam_status check_device_ptr(const roeam_grid *g, const void *p, const char *what)
+{
+    if (!p) return fail(ROEAM_E_ARG, "%s must be non-null", what);
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ROEAM_E_ARG, "%s is not a CUDA pointer", what);
+    }
+    if (at.type == cudaMemoryTypeManaged) return ROEAM_OK;
+    if (at.type != cudaMemoryTypeDevice || at.device != g->device)
+        return fail(ROEAM_E_ARG, "%s must be device memory of device %d", what, g->device);
+    if (((uintptr_t)p & 7) != 0) return fail(ROEAM_E_ARG, "%s must be 8-byte aligned", what);
+    return ROEAM_OK;
+}
+
+roeam_status roeam_set_state_device(roeam_grid *g, int grid_idx, const double *cons_dev, void *cuda_stream)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    CUDA_TRY(cudaSetDevice(g->device));
+    st = check_device_ptr(g, cons_dev, "cons_dev");
+    if (st != ROEAM_OK) return st;
+    const cudaStream_t cs = (cudaStream_t)cuda_stream;
+    return g->precision == 32 ? do_set_state_device<float>(g, grid_idx, cons_dev, cs)
+                              : do_set_state_device<double>(g, grid_idx, cons_dev, cs);
+}
+
+roeam_status roeam_get_state_device(roeam_grid *g, int grid_idx, double *cons_out_dev, void *cuda_stream)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    CUDA_TRY(cudaSetDevice(g->device));
+    st = check_device_ptr(g, cons_out_dev, "cons_out_dev");
+    if (st != ROEAM_OK) return st;
+    const cudaStream_t cs = (cudaStream_t)cuda_stream;
+    return g->precision == 32 ? do_get_state_device<float>(g, grid_idx, cons_out_dev, cs)
+                              : do_get_state_device<double>(g, grid_idx, cons_out_dev, cs);
 }
 
 roeam_status roeam_get_state(roeam_grid *g, int grid_idx, double *cons_out)
@@ -1157,8 +1260,8 @@ static __device__ __align__(256) unsigned char roeam_noalloc_scratch[NOALLOC_SCR
 namespace {
 
 // Device address of the scratch array on `device` (which must be current). The first call on
-// a device looks it up with cudaGetSymbolAddress; host code may not use the array's name as
-// an address.
+// a device (from roeam_create_grid) looks it up with cudaGetSymbolAddress, which loads the
+// module and commits the array there; host code may not use the array's name as an address.
 roeam_status noalloc_scratch(int device, void **out)
 {
     if (device < 0 || device >= 256) return fail(ROEAM_E_ARG, "device %d out of range", device);
@@ -1189,23 +1292,23 @@ roeam_status do_residual_noalloc(roeam_grid *g, int idx, double *out)
     roeam_status st = noalloc_scratch(g->device, &scratch);
     if (st != ROEAM_OK) return st;
     // The kernels address this grid at element offsets G.off (working-precision planes) and
-    // G.poff (float64 copy); shift the bases so that both land at the start of their regions.
-    const uintptr_t base_t = (uintptr_t)scratch - sizeof(T) * (uintptr_t)G.off;
-    const uintptr_t region_d = (uintptr_t)scratch + bytes_t;
-    const uintptr_t base_d = region_d - sizeof(double) * (uintptr_t)G.poff;
+    // G.poff (float64 copy); the shifts place both at the start of their scratch regions.
+    T *region_t = (T *)scratch;
+    double *region_d = (double *)((unsigned char *)scratch + bytes_t);
     StageArgs<T> a = base_args<T>(g);
     a.mode = MODE_RESIDUAL;
     a.src = (const T *)g->U;
     a.un = (const T *)g->U;
-    a.dst = (T *)base_t;
+    a.dst = region_t;
+    a.dst_shift = G.off;
     a.units = g->d_units_grid;
     a.tile_lo = g->h_tile_base[idx];
     a.tile_hi = g->h_tile_base[idx + 1];
     CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, g->stream));
-    CUDA_TRY(Launchers<T>::unpack(g->d_grids, idx, idx + 1, G.ni * G.nj, (const T *)base_t, (double *)base_d,
-                                  g->stream));
+    CUDA_TRY(Launchers<T>::unpack(g->d_grids, idx, idx + 1, G.ni * G.nj, region_t, region_d, g->stream, G.off,
+                                  G.poff));
     g->launches += 2;
-    CUDA_TRY(cudaMemcpyAsync(out, (const void *)region_d, bytes_d, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(out, region_d, bytes_d, cudaMemcpyDeviceToHost, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     return ROEAM_OK;
 }

@@ -39,6 +39,10 @@ __device__ __forceinline__ V2 operator-(V2 a) { return mk2(-a.v.x, -a.v.y); }
 __device__ __forceinline__ V2 vfma(V2 a, V2 b, V2 c) { V2 r; r.v = __ffma2_rn(a.v, b.v, c.v); return r; }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+// c - a b: one fused operation on scalars; on pairs the product and the packed subtraction.
+__device__ __forceinline__ float vfnma(float a, float b, float c) { return fmaf(-a, b, c); }
+__device__ __forceinline__ double vfnma(double a, double b, double c) { return fma(-a, b, c); }
+__device__ __forceinline__ V2 vfnma(V2 a, V2 b, V2 c) { return c - a * b; }
 
 template <typename V> struct Sc;
 template <> struct Sc<float> { using S = float; using M = bool; };
@@ -67,6 +71,11 @@ __device__ __forceinline__ B2 eq(V2 a, V2 b) { return {a.v.x == b.v.x, a.v.y == 
 __device__ __forceinline__ B2 operator&&(B2 a, B2 b) { return {a.x && b.x, a.y && b.y}; }
 template <typename T> __device__ __forceinline__ T sel(bool m, T a, T b) { return m ? a : b; }
 __device__ __forceinline__ V2 sel(B2 m, V2 a, V2 b) { return mk2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y); }
+
+// The 2D kernel translation units compile with -fmad=false: every fused multiply-add is
+// written out (vfma, vfnma), so a value comes out bit for bit the same wherever it is
+// evaluated (in a loop's prologue or body, in either copy of an unrolled body, in any work-unit
+// layout), and results do not depend on the tile shape or on how a grid is split into slabs.
 
 // Reciprocal, reciprocal square root and square root (of a non-negative value). FP32 uses
 // the single-instruction hardware approximations (PTX rcp/rsqrt/sqrt .approx). FP64 starts
@@ -137,10 +146,9 @@ template <typename V> __device__ __forceinline__ V fmach(V phi)
 {
     const V one = splat<V>(1);
     const V p = vmin(phi, splat<V>(2));
-    const V p2 = p * p;
-    const V t = one - p2;
+    const V t = vfnma(p, p, one);
     const V s = vfma(t, t, splat<V>(4));
-    const V q = one + p2;
+    const V q = vfma(p, p, one);
     return vmin(p * s * rsq(s * q * q), one);
 }
 
@@ -153,9 +161,9 @@ template <typename V> __device__ __forceinline__ V detector_of(V a)
 // Mirror image of a velocity about a unit normal (wall ghost state).
 template <typename T> __device__ __forceinline__ void mirror_vel(T &u, T &v, T nx, T ny)
 {
-    T un = u * nx + v * ny;
-    u -= T(2) * un * nx;
-    v -= T(2) * un * ny;
+    const T un2 = T(2) * vfma(u, nx, v * ny);
+    u = vfnma(un2, nx, u);
+    v = vfnma(un2, ny, v);
 }
 
 // ------------------------------------------------------------------ the Roe-AM flux
@@ -277,7 +285,7 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     // be copied onto it
     const V mn = vmin(Up, ch);
     const V smc = vcopysign(mn, uh) * chi;
-    const V pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmax(ch - Up, zero) * rh * du);
+    const V pp = vfma(smc, dp, vfma(s1, fM, one - s1) * vmax(ch - Up, zero) * rh * du);
     const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
     const V om = one - th;
     const V X = vfma(splat<V>(4) * c2h, th, om * om * uh * uh);
@@ -285,7 +293,7 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     const V ct = half * X * rX;    // c~
     const V Ut = half * (one + th) * uh;
     // U sgn(U~) min(|U~|, c~) = |U| min(|U~|, c~): U~ = (1 + theta) U / 2 has the sign of U
-    const V term = vfma(om, Up - aU * rX * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
+    const V term = vfma(om, vfnma(aU * rX, vmin(vabs(Ut), ct), Up), vmax(ct - Up, zero));
     V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
     if constexpr (ABL) {
         if (var.dup_mode == 1) A = zero;
@@ -503,8 +511,8 @@ __device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> 
         for (int k = 0; k < 4; ++k) {
             lL[k] = limiter(vanleer, WL[k] - M0[k], WR[k] - WL[k]);
             lR[k] = limiter(vanleer, WR[k] - WL[k], M3[k] - WR[k]);
-            rL[k] = WL[k] + T(0.5) * lL[k];
-            rR[k] = WR[k] - T(0.5) * lR[k];
+            rL[k] = vfma(T(0.5), lL[k], WL[k]);
+            rR[k] = vfnma(T(0.5), lR[k], WR[k]);
         }
         // Positivity of the reconstructed density and pressure, else first order. In FP32 a
         // density or pressure that comes out within rounding of zero (or below it) is
@@ -518,8 +526,8 @@ __device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> 
                 double dL[4], dR[4];
                 for (int k = 0; k < 4; ++k) {
                     const double wl = WL[k], wr = WR[k], m0 = M0[k], m3 = M3[k];
-                    dL[k] = wl + 0.5 * limiter(vanleer, wl - m0, wr - wl);
-                    dR[k] = wr - 0.5 * limiter(vanleer, wr - wl, m3 - wr);
+                    dL[k] = fma(0.5, limiter(vanleer, wl - m0, wr - wl), wl);
+                    dR[k] = fma(-0.5, limiter(vanleer, wr - wl, m3 - wr), wr);
                 }
                 pos = dL[0] > 0.0 && dL[3] > 0.0 && dR[0] > 0.0 && dR[3] > 0.0;
                 if (pos)
@@ -540,8 +548,8 @@ __device__ __forceinline__ void face_scalar(const Face<T> &f, const GridCoef<T> 
     roeam_flux2<ABL>(L, R, f.s1, K, eps1, xi_form, G2, var);
     const T h = T(0.5) * f.len;
     F[0] = h * G2[0];
-    F[1] = h * (f.nx * G2[1] - f.ny * G2[2]);
-    F[2] = h * (f.ny * G2[1] + f.nx * G2[2]);
+    F[1] = h * vfnma(f.ny, G2[2], f.nx * G2[1]);
+    F[2] = h * vfma(f.ny, G2[1], f.nx * G2[2]);
     F[3] = h * G2[3];
 }
 
@@ -588,10 +596,10 @@ __device__ __forceinline__ void faces_packed(const Face<float> &fx, const Face<f
     Fy[0] = hy * G2[0].v.y;
     Fy[3] = hy * G2[3].v.y;
     if constexpr (CURV) {
-        Fx[1] = hx * (fx.nx * G2[1].v.x - fx.ny * G2[2].v.x);
-        Fx[2] = hx * (fx.ny * G2[1].v.x + fx.nx * G2[2].v.x);
-        Fy[1] = hy * (fy.nx * G2[1].v.y - fy.ny * G2[2].v.y);
-        Fy[2] = hy * (fy.ny * G2[1].v.y + fy.nx * G2[2].v.y);
+        Fx[1] = hx * vfnma(fx.ny, G2[2].v.x, fx.nx * G2[1].v.x);
+        Fx[2] = hx * vfma(fx.ny, G2[1].v.x, fx.nx * G2[2].v.x);
+        Fy[1] = hy * vfnma(fy.ny, G2[2].v.y, fy.nx * G2[1].v.y);
+        Fy[2] = hy * vfma(fy.ny, G2[1].v.y, fy.nx * G2[2].v.y);
     } else {
         Fx[1] = hx * G2[1].v.x;
         Fx[2] = hx * G2[2].v.x;
@@ -663,7 +671,7 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
     } else {
         const T ri = rcp(q.raw[0]);
         c.r = q.raw[0]; c.u = q.raw[1] * ri; c.v = q.raw[2] * ri;
-        c.p = K.gm1 * (q.raw[3] - T(0.5) * q.raw[0] * (c.u * c.u + c.v * c.v));
+        c.p = K.gm1 * vfnma(T(0.5) * q.raw[0], vfma(c.u, c.u, c.v * c.v), q.raw[3]);
         if constexpr (WALLS) {
             if constexpr (LATE_SOLID) { if (R.solid && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1; }
             else if (q.solid) c.fl = 1;
@@ -675,7 +683,7 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
             if constexpr (CURV) {
                 const int b = (j < 0 ? 0 : R.nj) * R.vpitch + isrc;
                 const T sx = -(R.vdy[b + 1] - R.vdy[b]), sy = K.dx + (R.vdx[b + 1] - R.vdx[b]);
-                const T l = rsq(sx * sx + sy * sy);
+                const T l = rsq(vfma(sx, sx, sy * sy));
                 nx = sx * l; ny = sy * l;
             }
             mirror_vel(c.u, c.v, nx, ny);
@@ -685,7 +693,7 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
             if constexpr (CURV) {
                 const int b = clampi(j, 0, R.nj - 1) * R.vpitch + (i < 0 ? 0 : R.ni);
                 const T sx = K.dy + (R.vdy[b + R.vpitch] - R.vdy[b]), sy = -(R.vdx[b + R.vpitch] - R.vdx[b]);
-                const T l = rsq(sx * sx + sy * sy);
+                const T l = rsq(vfma(sx, sx, sy * sy));
                 nx = sx * l; ny = sy * l;
             }
             mirror_vel(c.u, c.v, nx, ny);
@@ -740,7 +748,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         GridRegs<T> R;
         R.src = a.src + G.off;
         R.un = a.un + G.off;
-        R.dst = a.dst + G.off;
+        R.dst = a.dst + (G.off - a.dst_shift);
         R.ni = G.ni; R.nj = G.nj; R.pitch = G.pitch; R.plane = (int)G.plane;
         R.bcW = G.bc[0]; R.bcE = G.bc[1]; R.bcS = G.bc[2]; R.bcN = G.bc[3];
         if constexpr (CURV) { R.vdx = a.vdx + G.voff; R.vdy = a.vdy + G.voff; R.vpitch = G.vpitch; }
@@ -870,12 +878,12 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             if constexpr (CURV) {
                 // x-face: vertices (i, j), (i, j+1); y-face: vertices (i, j), (i+1, j)
                 T sx = K.dy + (vY[2] - vY[1]), sy = -(vX[2] - vX[1]);
-                fx.len = sqrt0(sx * sx + sy * sy);
+                fx.len = sqrt0(vfma(sx, sx, sy * sy));
                 T li = rcp(fx.len);
                 fx.nx = sx * li; fx.ny = sy * li;
                 const T xr = shdn(vX[1], 1), yr = shdn(vY[1], 1);
                 sx = -(yr - vY[1]); sy = K.dx + (xr - vX[1]);
-                fy.len = sqrt0(sx * sx + sy * sy);
+                fy.len = sqrt0(vfma(sx, sx, sy * sy));
                 li = rcp(fy.len);
                 fy.nx = sx * li; fy.ny = sy * li;
                 if constexpr (!MUSCL) {
@@ -936,9 +944,9 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     fx.nAmx = shup(fx.nx, 1); fx.nAmy = shup(fx.ny, 1);
                     fx.nBpx = shdn(fx.nx, 1); fx.nBpy = shdn(fx.ny, 1);
                     const T x0 = shdn(vX[0], 1), y0 = shdn(vY[0], 1), x3 = shdn(vX[3], 1), y3 = shdn(vY[3], 1);
-                    T tx = -(y0 - vY[0]), ty = K.dx + (x0 - vX[0]), l = rsq(tx * tx + ty * ty);
+                    T tx = -(y0 - vY[0]), ty = K.dx + (x0 - vX[0]), l = rsq(vfma(tx, tx, ty * ty));
                     fy.nAmx = tx * l; fy.nAmy = ty * l;
-                    tx = -(y3 - vY[3]); ty = K.dx + (x3 - vX[3]); l = rsq(tx * tx + ty * ty);
+                    tx = -(y3 - vY[3]); ty = K.dx + (x3 - vX[3]); l = rsq(vfma(tx, tx, ty * ty));
                     fy.nBpx = tx * l; fy.nBpy = ty * l;
                 }
                 if constexpr (!PACKED || WALLS || MUSCL) {
@@ -971,8 +979,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                         T out[4];
                         for (int k = 0; k < 4; ++k) {
                             // U^(k) of this cell, loaded rows ago (mostly an L1 hit) or above
-                            const T upd = (MUSCL && CURV ? Uk[k] : __ldg(R.src + x + k * R.plane)) + dt * Rs[k];
-                            out[k] = combine ? a.alpha * Un[k] + a.beta * upd : upd;
+                            const T upd = vfma(dt, Rs[k], MUSCL && CURV ? Uk[k] : __ldg(R.src + x + k * R.plane));
+                            out[k] = combine ? vfma(a.alpha, Un[k], a.beta * upd) : upd;
                         }
                         for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = out[k];
                         if (!solid && a.want_rate) {
@@ -987,7 +995,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                             // p > 0 without the division: 2 rho (rho E) > (rho u)^2 + (rho v)^2; a cell
                             // that fails it (rare: also products beyond the FP32 range) is decided
                             // by its pressure
-                            const T e2 = T(2) * out[0] * out[3], m2 = out[1] * out[1] + out[2] * out[2];
+                            const T e2 = T(2) * out[0] * out[3], m2 = vfma(out[1], out[1], out[2] * out[2]);
                             if (!(out[0] > T(0)) || !(e2 > m2)) {
                                 const CellPrims<T> cp = cell_prims(out[0], out[1], out[2], out[3], K);
                                 if (!(out[0] > T(0)) || !(cp.p > T(0))) {
@@ -1001,7 +1009,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     } else if (!solid) {
                         for (int k = 0; k < 4; ++k) {
                             const double rk = (double)Rs[k];
-                            acc_s[k] += rk * rk;
+                            acc_s[k] = fma(rk, rk, acc_s[k]);
                             acc_m[k] = fmax(acc_m[k], fabs(rk));
                         }
                     }
@@ -1098,26 +1106,28 @@ __global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, const G
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) pack_kernel(const GridDev *grids, int g_lo, const double *packed, T *U)
+__global__ void __launch_bounds__(256) pack_kernel(const GridDev *grids, int g_lo, const double *packed, T *U,
+                                                   long long p_shift)
 {
     const GridDev &G = grids[g_lo + blockIdx.y];
     const long long n = (long long)G.ni * G.nj;
     for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
         const int i = (int)(q % G.ni), j = (int)(q / G.ni);
         const long long c = G.off + (long long)j * G.pitch + i;
-        for (int k = 0; k < 4; ++k) U[c + k * G.plane] = T(packed[G.poff + k * n + q]);
+        for (int k = 0; k < 4; ++k) U[c + k * G.plane] = T(packed[G.poff - p_shift + k * n + q]);
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g_lo, const T *U, double *packed)
+__global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g_lo, const T *U, double *packed,
+                                                     long long u_shift, long long p_shift)
 {
     const GridDev &G = grids[g_lo + blockIdx.y];
     const long long n = (long long)G.ni * G.nj;
     for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
         const int i = (int)(q % G.ni), j = (int)(q / G.ni);
-        const long long c = G.off + (long long)j * G.pitch + i;
-        for (int k = 0; k < 4; ++k) packed[G.poff + k * n + q] = (double)U[c + k * G.plane];
+        const long long c = G.off - u_shift + (long long)j * G.pitch + i;
+        for (int k = 0; k < 4; ++k) packed[G.poff - p_shift + k * n + q] = (double)U[c + k * G.plane];
     }
 }
 
@@ -1144,7 +1154,7 @@ __global__ void __launch_bounds__(256) totals_kernel(const GridDev *grids, const
             V = G.dx * G.dy;
         }
         const long long c = G.off + (long long)j * G.pitch + i;
-        for (int k = 0; k < 4; ++k) s[k] += V * (double)U[c + k * G.plane];
+        for (int k = 0; k < 4; ++k) s[k] = fma(V, (double)U[c + k * G.plane], s[k]);
     }
     for (int o = 16; o > 0; o >>= 1)
         for (int k = 0; k < 4; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
@@ -1243,23 +1253,23 @@ cudaError_t Launchers<T>::rate(const GridDev *grids, const GridCoef<T> *coef, in
 
 template <typename T>
 cudaError_t Launchers<T>::pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
-                               cudaStream_t s)
+                               cudaStream_t s, long long p_shift)
 {
     if (g_hi <= g_lo) return cudaSuccess;
     int bx = (max_cells + 255) / 256;
     bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
-    pack_kernel<T><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, packed, U);
+    pack_kernel<T><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, packed, U, p_shift);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launchers<T>::unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, double *packed,
-                                 cudaStream_t s)
+                                 cudaStream_t s, long long u_shift, long long p_shift)
 {
     if (g_hi <= g_lo) return cudaSuccess;
     int bx = (max_cells + 255) / 256;
     bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
-    unpack_kernel<T><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, U, packed);
+    unpack_kernel<T><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, U, packed, u_shift, p_shift);
     return cudaGetLastError();
 }
 

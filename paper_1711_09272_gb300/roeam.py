@@ -22,7 +22,8 @@ STATUS_NAMES = ["OK", "E_ARG", "E_CUDA", "E_OOM", "E_NONPOSITIVE", "E_NONFINITE"
 ROEAM_NORM_L2, ROEAM_NORM_LINF = 0, 1
 
 # Entry points declared in include/roeam.h (checked by the tests).
-EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual",
+EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_get_state", "roeam_set_state_device",
+           "roeam_get_state_device", "roeam_flux_residual",
            "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
            "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
            "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc",
@@ -76,6 +77,8 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_destroy_grid.restype = None
     lib.roeam_set_state.argtypes = [vp, C.c_int, vp]
     lib.roeam_get_state.argtypes = [vp, C.c_int, vp]
+    lib.roeam_set_state_device.argtypes = [vp, C.c_int, vp, vp]
+    lib.roeam_get_state_device.argtypes = [vp, C.c_int, vp, vp]
     lib.roeam_flux_residual.argtypes = [vp, C.c_int, vp]
     lib.roeam_rk_step.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp]
     lib.roeam_residual_norm.argtypes = [vp, C.c_int, C.c_int, dp]
@@ -109,7 +112,8 @@ def load_library(path: str = LIB_PATH):
     lib.roeam3_check.argtypes = [vp]
     lib.roeam3_launch_count.argtypes = [vp]
     lib.roeam3_launch_count.restype = C.c_ulonglong
-    for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_flux_residual", "roeam_rk_step",
+    for name in ("roeam_create_grid", "roeam_set_state", "roeam_get_state", "roeam_set_state_device",
+                 "roeam_get_state_device", "roeam_flux_residual", "roeam_rk_step",
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
                  "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam_rk_stage",
                  "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check", "roeam_step_host",
@@ -152,6 +156,18 @@ def roeam_set_state(h: int, grid_idx: int, cons) -> None:
 
 def roeam_get_state(h: int, grid_idx: int, out) -> None:
     _check(load_library().roeam_get_state(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(out))))
+
+
+def roeam_set_state_device(h: int, grid_idx: int, cons_dev: int, cuda_stream: int = 0) -> None:
+    """cons_dev: address of float64 device memory ([4][nj][ni] per grid); cuda_stream orders
+    the call with the caller's work (include/roeam.h)."""
+    _check(load_library().roeam_set_state_device(C.c_void_p(h), grid_idx, C.c_void_p(cons_dev),
+                                                 C.c_void_p(cuda_stream or None)))
+
+
+def roeam_get_state_device(h: int, grid_idx: int, cons_out_dev: int, cuda_stream: int = 0) -> None:
+    _check(load_library().roeam_get_state_device(C.c_void_p(h), grid_idx, C.c_void_p(cons_out_dev),
+                                                 C.c_void_p(cuda_stream or None)))
 
 
 def roeam_flux_residual(h: int, grid_idx: int, out=None) -> None:
@@ -328,6 +344,17 @@ class Batch:
     def set_states(self, Us):
         packed = np.concatenate([np.ascontiguousarray(U, dtype=np.float64).ravel() for U in Us])
         roeam_set_state(self.handle, -1, packed)
+
+    def set_state_device(self, U, grid_idx: int = 0, stream: int = 0):
+        """U: a contiguous float64 CUDA tensor (or any object with data_ptr()) holding grid
+        grid_idx's state (all grids, concatenated, with -1); stream: a cudaStream_t handle
+        (e.g. torch.cuda.current_stream().cuda_stream) that the call is ordered with."""
+        roeam_set_state_device(self.handle, grid_idx, U.data_ptr(), stream)
+
+    def get_state_device(self, out, grid_idx: int = 0, stream: int = 0):
+        """Writes the state into the float64 CUDA tensor `out` (ordered on `stream`)."""
+        roeam_get_state_device(self.handle, grid_idx, out.data_ptr(), stream)
+        return out
 
     def get_state(self, grid_idx: int = 0) -> np.ndarray:
         out = np.empty(self._shape(grid_idx))

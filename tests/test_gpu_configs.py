@@ -65,11 +65,14 @@ def check_cells(spec, U0, U1, dt, cells, tol):
     return worst
 
 
-def test_batch_full_size_sampled_parity():
-    """The batched FP32 workload (512 grids) after 20 steps: sampled cells of step 21."""
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+def test_batch_full_size_sampled_parity(cfg):
+    """The batched FP32 workload (512 grids) after 20 steps: sampled cells of step 21, with
+    each work-unit shape the autotuner can pick for it."""
     specs, states = W.batch(512)
-    rng = W.SplitMix64(99)
+    rng = W.SplitMix64(99 + cfg)
     with P().Batch(specs, precision=32) as b:
+        b.set_tile_config(cfg)
         b.set_states(states)
         b.step(0.5, nsteps=20)
         U0 = b.get_states()

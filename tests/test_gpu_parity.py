@@ -16,6 +16,9 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = {64: 1e-12, 32: 1e-5}
+# every work-unit shape the library is built with (roeam_tile_config_count() == 4); the
+# autotuner may pick any of them for a run
+TILE_CFGS = [0, 1, 2, 3]
 
 
 def P():
@@ -32,10 +35,13 @@ def rel_state_err(Ug, Uo):
     return float(np.max(np.abs(Ug - Uo).reshape(4, -1).max(axis=1) / state_scale(Uo)))
 
 
-def one_step_parity(spec, U, prec, cfl=0.5, dt_fixed=0.0, **variant):
+def one_step_parity(spec, U, prec, cfl=0.5, dt_fixed=0.0, cfg=0, **variant):
     """Sets U on the GPU, reads back the (rounded) device state, advances one step on both
-    sides from that same state and returns the relative state error."""
+    sides from that same state and returns the relative state error. cfg selects the
+    stage kernel's work-unit shape."""
     with P().Batch([spec], precision=prec) as b:
+        assert P().roeam_tile_config_count() == len(TILE_CFGS)
+        b.set_tile_config(cfg)
         b.set_state(U, 0)
         U0 = b.get_state(0)
         b.step(cfl=cfl, dt_fixed=dt_fixed, nsteps=1)
@@ -67,12 +73,13 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("cfg", TILE_CFGS)
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_step_parity_rough_states(case, prec):
+def test_step_parity_rough_states(case, prec, cfg):
     spec, mach = CASES[case]()
     U = W.random_rough_state(spec, seed=101, mach=mach, jump=0.4)
-    err = one_step_parity(spec, U, prec)
+    err = one_step_parity(spec, U, prec, cfg=cfg)
     assert err <= TOL[prec], err
 
 
@@ -306,17 +313,19 @@ def test_step_host_matches_separate_calls(prec):
     assert np.array_equal(buf, ref)
 
 
+@pytest.mark.parametrize("cfg", TILE_CFGS)
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("shape", [(4, 4), (5, 7), (31, 4), (33, 5), (4, 65), (61, 6)])
-def test_tiny_and_tile_edge_grids(shape, prec):
+@pytest.mark.parametrize("shape", [(4, 4), (5, 7), (31, 4), (33, 5), (4, 65), (61, 6), (29, 129)])
+def test_tiny_and_tile_edge_grids(shape, prec, cfg):
     """The smallest grids and sizes at the strip / segment edges (30 or 28 written columns per
-    strip, segments of 32 rows): periodic and wall/inflow/outflow, first order and van Leer."""
+    strip, segments of 16 to 128 rows, halved down to 4 rows for a single small grid):
+    periodic and wall/inflow/outflow, first order and van Leer, every work-unit shape."""
     ni, nj = shape
     for bc, recon in (((W.PERIODIC,) * 4, 0), ((W.INFLOW, W.OUTFLOW, W.WALL, W.WALL), 2)):
         spec = W.GridSpec(ni=ni, nj=nj, dx=0.1, dy=0.1, bc=bc, inflow=(1.1, 0.4, 0.0, 1.0),
                           params=W.SchemeParams(m_ref=0.4, recon=recon))
         U = W.random_rough_state(spec, seed=ni * 100 + nj, mach=0.8, jump=0.3)
-        assert one_step_parity(spec, U, prec, cfl=0.4) <= TOL[prec], (bc, recon)
+        assert one_step_parity(spec, U, prec, cfl=0.4, cfg=cfg) <= TOL[prec], (bc, recon)
 
 
 def test_largest_batch_count():
@@ -351,3 +360,48 @@ def test_tiny_magnitudes(recon):
     spec = W.GridSpec(ni=40, nj=24, dx=0.02, dy=0.02, params=W.SchemeParams(m_ref=0.5, recon=recon))
     U = W.random_smooth_state(spec, seed=5, mach=0.5, amp=0.2) * 1e-24
     assert one_step_parity(spec, U, 32) <= TOL[32]
+
+
+def _run_all_shapes(specs, states, prec, nsteps):
+    outs, dts = [], []
+    for cfg in TILE_CFGS:
+        with P().Batch(specs, precision=prec) as b:
+            b.set_tile_config(cfg)
+            b.set_states(states)
+            b.step(0.5, nsteps=nsteps - 1)
+            dts.append(b.step(0.5, nsteps=1, want_dt=True))
+            outs.append(b.get_states())
+    return outs, dts
+
+
+@pytest.mark.parametrize("kind", ["batch_first", "batch_vanleer_fp64", "walls_minmod", "warped_step", "ablation_mixed"])
+def test_results_independent_of_tile_shape(kind):
+    """The same state stepped with every work-unit shape (segments of 16, 32, 64 and 128 rows,
+    so that a row sits at different places within its unit and is evaluated by different
+    copies of the unrolled loop body) gives bit-identical states and time steps: the kernels'
+    fused multiply-adds are all explicit, so the autotuner's choice cannot change a result."""
+    if kind == "batch_first":
+        specs, states = W.batch(512)
+        prec, n = 32, 6
+    elif kind == "batch_vanleer_fp64":
+        specs, states = W.batch(160, seed=5)
+        specs = [W.with_params(s, recon=2) for s in specs]
+        prec, n = 64, 3
+    elif kind == "walls_minmod":
+        from dataclasses import replace
+        specs, states = W.batch(256, seed=7)
+        specs = [replace(W.with_params(s, recon=1), bc=(W.OUTFLOW, W.OUTFLOW, W.WALL, W.WALL)) if k % 3 == 0
+                 else W.with_params(s, recon=1) for k, s in enumerate(specs)]
+        prec, n = 32, 3
+    elif kind == "warped_step":
+        spec, U = W.warped_step(2048, 2048)
+        specs, states, prec, n = [spec], [U], 32, 3
+    else:
+        specs, states = W.batch(256, seed=9)
+        specs = [W.with_params(s, scheme=1, harten=0.1) if k % 2 else s for k, s in enumerate(specs)]
+        prec, n = 32, 3
+    outs, dts = _run_all_shapes(specs, states, prec, n)
+    for cfg in TILE_CFGS[1:]:
+        assert np.array_equal(dts[cfg], dts[0]), cfg
+        for g in range(len(specs)):
+            assert np.array_equal(outs[cfg][g], outs[0][g]), (cfg, g)
