@@ -241,10 +241,16 @@ roeam_status roeam_check(roeam_grid *g);
  * on the GPU race. Synchronises. */
 roeam_status roeam_flux_residual_noalloc(roeam_grid *g, int grid_idx, double *res_out);
 
-/* Number of tile shapes (stage-kernel variants) the library is built with. */
+/* Number of tile shapes (stage-kernel work-unit layouts and schedules) the library is built
+ * with: 10. Shapes 0-4 cut each grid into warp strips of 32 lanes and segments of 32, 64, 16,
+ * 128 and 256 rows and let warps claim units dynamically in the order of the unit table
+ * (tallest first); shapes 5-9 are the same heights with a static round robin of units over
+ * warps. (Kernels that do not claim units dynamically treat 0-4 as 5-9; a batch too small to
+ * give every resident warp a unit halves the height down to 4 rows.) Results are bit-identical
+ * across shapes. */
 int roeam_tile_config_count(void);
 
-/* Describes tile shape `cfg`: tile width tx, height ty (cells) and threads per CTA. */
+/* Describes tile shape `cfg`: strip width tx, segment height ty (cells) and threads per CTA. */
 roeam_status roeam_tile_config_info(int cfg, int *tx, int *ty, int *threads);
 
 /* Selects tile shape `cfg` for this handle's stage kernels (default 0). Captured graphs
@@ -252,9 +258,13 @@ roeam_status roeam_tile_config_info(int cfg, int *tx, int *ty, int *threads);
 roeam_status roeam_set_tile_config(roeam_grid *g, int cfg);
 
 /* Autotuner: times `steps` SSP-RK3 steps at `cfl` with every tile shape on the current
- * state, restores the state after each trial, and keeps the fastest shape. best_cfg
- * (nullable) receives it; ms_per_step (nullable, roeam_tile_config_count() doubles) the
- * measured time per step of each shape. Synchronises; allocates a temporary copy of the state. */
+ * state (best of two timings; shapes that give the same units and schedule are timed once),
+ * restores the state after each trial, and keeps the fastest shape. best_cfg (nullable)
+ * receives it; ms_per_step (nullable, roeam_tile_config_count() doubles) the measured time
+ * per step of each shape. The result is kept for the process: a later call on any handle
+ * with the same workload (device, kernel family, every grid's sizes, boundary kinds and
+ * scheme switches) applies it without timing and returns the same figures. Synchronises;
+ * allocates a temporary copy of the state when it times. */
 roeam_status roeam_autotune(roeam_grid *g, double cfl, int steps, int *best_cfg, double *ms_per_step);
 
 /* Number of kernels this handle has launched (graph nodes count one each per replay). */

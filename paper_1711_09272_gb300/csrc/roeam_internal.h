@@ -70,6 +70,10 @@ struct StageArgs {
     T cfl_t, dt_fixed_t;    // the same in the working precision
     unsigned *status;
     double *partials;       // MODE_NORM: gridDim.x * 8 (sum R^2 [4], max |R| [4])
+    // Dynamic unit scheduling (null: static round robin): work[0] counts the units claimed past
+    // each warp's first, work[1] the warps that have finished; the last warp to finish resets
+    // both, so that the next launch on the handle's stream starts from zero.
+    unsigned *work;
 };
 
 // Work-unit shapes of the stage kernel: a warp sweeps a strip tx = 32 lanes wide (2H of
@@ -95,10 +99,17 @@ constexpr int stage_min_blocks()
 {
     return (sizeof(T) != 4 || ABL) ? 1 : ((!MUSCL && !CURV) ? STAGE_MIN_BLOCKS_FAST : STAGE_MIN_BLOCKS_OTHER);
 }
-struct TileCfg { int tx, ty, nt; };
-constexpr int NUM_TILE_CFGS = 4;
-constexpr TileCfg TILE_CFGS[NUM_TILE_CFGS] = {{32, 32, STAGE_THREADS}, {32, 64, STAGE_THREADS},
-                                              {32, 16, STAGE_THREADS}, {32, 128, STAGE_THREADS}};
+// dyn: dynamic unit scheduling (the kernels that support it claim units from a counter after
+// their first; 0 = static round robin over the unit table).
+struct TileCfg { int tx, ty, nt, dyn; };
+constexpr int NUM_TILE_CFGS = 10;
+constexpr TileCfg TILE_CFGS[NUM_TILE_CFGS] = {
+    {32, 32, STAGE_THREADS, 1}, {32, 64, STAGE_THREADS, 1}, {32, 16, STAGE_THREADS, 1}, {32, 128, STAGE_THREADS, 1},
+    {32, 256, STAGE_THREADS, 1}, {32, 32, STAGE_THREADS, 0}, {32, 64, STAGE_THREADS, 0}, {32, 16, STAGE_THREADS, 0},
+    {32, 128, STAGE_THREADS, 0}, {32, 256, STAGE_THREADS, 0}};
+// Whether a stage-kernel family claims units dynamically when asked to (the reconstructing
+// curvilinear kernels keep the static round robin).
+__host__ __device__ constexpr bool stage_dynamic(int muscl, int curv) { return !(muscl && curv); }
 
 // Stage-kernel families: no walls anywhere in the batch; some WALL side or solid cells; some
 // grid uses an ablation variant of the flux (every face on the scalar path).

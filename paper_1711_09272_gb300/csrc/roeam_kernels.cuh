@@ -152,10 +152,17 @@ template <typename V> __device__ __forceinline__ V fmach(V phi)
     return vmin(p * s * rsq(s * q * q), one);
 }
 
-// Eq. 95 (with P values of Eq. 97 already reduced to their minimum a by Eq. 96).
+// Eq. 95 (with P values of Eq. 97 already reduced to their minimum a by Eq. 96). The
+// argument is a ratio of positive values (at most 1, plus the rounding of a reciprocal), so
+// Eq. 98 needs no clamp of its argument here; its result is still clamped at 1.
 template <typename V> __device__ __forceinline__ V detector_of(V a)
 {
-    return sel(ge(a, splat<V>(1)), splat<V>(1), pow8(fmach(a)));
+    const V one = splat<V>(1);
+    const V t = vfnma(a, a, one);
+    const V s = vfma(t, t, splat<V>(4));
+    const V q = vfma(a, a, one);
+    const V f = vmin(a * s * rsq(s * q * q), one);
+    return sel(ge(a, one), one, pow8(f));
 }
 
 // Mirror image of a velocity about a unit normal (wall ghost state).
@@ -440,9 +447,12 @@ template <typename V> __device__ __forceinline__ V limiter(bool vanleer, V a, V 
 }
 
 // Cell-window entry: primitives (rho, u, v, p) in the global frame, the derived face
-// quantities (first order: computed once per cell), and the flags (bit 0 solid, bit 1 wall).
+// quantities (first order: computed once per cell), the conserved rho u, rho v, rho E as
+// loaded (the first-order kernels' stage epilogue takes U^(k) from here instead of reading it
+// again), and the flags (bit 0 solid, bit 1 wall).
 template <typename T> struct WC {
     T r, u, v, p, c2, H, sr, Mq;
+    T q1, q2, q3;
     uint8_t fl;
 };
 
@@ -668,9 +678,11 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
     c.fl = 0;
     if (kx == 2 || ky == 2) {
         c.r = K.inflow[0]; c.u = K.inflow[1]; c.v = K.inflow[2]; c.p = K.inflow[3];
+        // (q1..q3 stay unset: an inflow ghost cell is never written)
     } else {
         const T ri = rcp(q.raw[0]);
         c.r = q.raw[0]; c.u = q.raw[1] * ri; c.v = q.raw[2] * ri;
+        c.q1 = q.raw[1]; c.q2 = q.raw[2]; c.q3 = q.raw[3];
         c.p = K.gm1 * vfnma(T(0.5) * q.raw[0], vfma(c.u, c.u, c.v * c.v), q.raw[3]);
         if constexpr (WALLS) {
             if constexpr (LATE_SOLID) { if (R.solid && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1; }
@@ -709,6 +721,7 @@ template <bool WALLS, typename T> __device__ __forceinline__ WC<T> shup_c(const 
     o.r = shup(c.r, d); o.u = shup(c.u, d); o.v = shup(c.v, d); o.p = shup(c.p, d);
     if (derived) { o.c2 = shup(c.c2, d); o.H = shup(c.H, d); o.sr = shup(c.sr, d); o.Mq = shup(c.Mq, d); }
     else { o.c2 = o.H = o.sr = o.Mq = T(0); }
+    // (q1..q3 stay unset: a neighbour's conserved values are never read)
     o.fl = WALLS ? (uint8_t)__shfl_up_sync(0xffffffffu, (int)c.fl, d) : (uint8_t)0;
     return o;
 }
@@ -719,6 +732,31 @@ template <bool WALLS, typename T> __device__ __forceinline__ WC<T> shdn_c(const 
     o.c2 = o.H = o.sr = o.Mq = T(0);
     o.fl = WALLS ? (uint8_t)__shfl_down_sync(0xffffffffu, (int)c.fl, d) : (uint8_t)0;
     return o;
+}
+
+// Dynamic unit scheduling (StageArgs::work): the unit after u for this warp. DYN = false keeps
+// the static round robin (the reconstructing curvilinear kernels: their units are of equal size
+// on the grids they serve, and the claim's registers made them spill, -16 % on the warped step).
+template <bool DYN, typename T>
+__device__ __forceinline__ int next_unit(const StageArgs<T> &a, int u, int nwarps, int lane)
+{
+    if (!DYN || !a.work) return u + nwarps;
+    unsigned n = 0;
+    if (lane == 0) n = atomicAdd(a.work, 1u);
+    return a.tile_lo + nwarps + (int)__shfl_sync(0xffffffffu, n, 0);
+}
+// A warp that has run out of units counts itself done; the last one resets the counters (every
+// warp's final claim precedes its count, fenced).
+template <bool DYN, typename T>
+__device__ __forceinline__ void finish_units(const StageArgs<T> &a, int nwarps, int lane)
+{
+    if (!DYN || !a.work || lane != 0) return;
+    __threadfence();
+    if (atomicAdd(a.work + 1, 1u) == (unsigned)nwarps - 1u) {
+        __threadfence();
+        atomicExch(a.work, 0u);
+        atomicExch(a.work + 1, 0u);
+    }
 }
 
 template <typename T, bool MUSCL, bool CURV, bool WALLS, int NT, bool ABL>
@@ -738,7 +776,11 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
 
     double acc_s[4] = {0.0, 0.0, 0.0, 0.0}, acc_m[4] = {0.0, 0.0, 0.0, 0.0};
 
-    for (int u = a.tile_lo + warp; u < a.tile_hi; u += nwarps) {
+    // Each warp takes unit tile_lo + warp first, then (dynamic scheduling) the next unclaimed
+    // one, in the order of the unit table (whole-batch launches: by decreasing height), so that
+    // warps that drew short units take more of them and the launch ends evenly.
+    constexpr bool DYN = stage_dynamic(MUSCL, CURV);
+    for (int u = a.tile_lo + warp; u < a.tile_hi; u = next_unit<DYN>(a, u, nwarps, lane)) {
         const int4 unit = __ldg(a.units + u);   // (grid, first lane's column, j0, j1)
         const int g = unit.x;
         const int i = unit.y + lane;            // this lane's column
@@ -977,9 +1019,16 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     const int x = (j - 1) * R.pitch + i;
                     if (stage_mode) {
                         T out[4];
+                        const WC<T> &self = Wn[H - 1];
+                        const T Uw[4] = {self.r, self.q1, self.q2, self.q3};
                         for (int k = 0; k < 4; ++k) {
-                            // U^(k) of this cell, loaded rows ago (mostly an L1 hit) or above
-                            const T upd = vfma(dt, Rs[k], MUSCL && CURV ? Uk[k] : __ldg(R.src + x + k * R.plane));
+                            // U^(k) of this cell: kept in the window (FP32 first order without
+                            // walls, +1.2 % on the benchmark batch; the walls and FP64 kernels then
+                            // spill), loaded above (reconstructing curvilinear), or loaded again
+                            // (mostly an L1 hit)
+                            const T uk = (!MUSCL && !WALLS && sizeof(T) == 4) ? Uw[k]
+                                                            : ((MUSCL && CURV) ? Uk[k] : __ldg(R.src + x + k * R.plane));
+                            const T upd = vfma(dt, Rs[k], uk);
                             out[k] = combine ? vfma(a.alpha, Un[k], a.beta * upd) : upd;
                         }
                         for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = out[k];
@@ -1036,6 +1085,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             if (lane == 0 && my_rate > T(0)) atomicMax(a.rate_wr + g, rate_bits(my_rate));
         }
     }
+
+    finish_units<DYN>(a, nwarps, lane);
 
     if (a.mode == MODE_NORM) {
         // Fixed-order block reduction of the FP64 partials: warp shuffles, then warp 0.
