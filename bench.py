@@ -7,9 +7,14 @@ dt; all grids advance in one persistent launch per Runge-Kutta stage, replayed f
 captured CUDA graph. Metric: cell-updates per second per RK stage (whole job).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batch|warped-slabs]
 
-Under torchrun (N > 1) every rank advances its own seeded batch (weak scaling, no
-data-path collective); rank 0 prints one JSON line with the max-over-ranks time.
+With N > 1 every rank advances its own seeded batch (weak scaling, no data-path collective);
+rank 0 prints one JSON line with the max-over-ranks time. Under torchrun the ranks come from
+the environment (WORLD_SIZE must equal N); without it bench.py starts N ranks itself, one per
+GPU, over NCCL. `--workload warped-slabs` times the 4096 x 4096 curvilinear workload split
+into N row slabs, one per rank, with the ghost rows exchanged over NCCL in device memory
+while each slab's interior is computed (strong scaling: the grid is fixed).
 `--impl reference` times the CPU oracle (the FP64 C program under oracle/) on a bounded
 sample of the same workload on this host's cores.
 """
@@ -542,6 +547,75 @@ def run_ours(args):
     return 0
 
 
+def run_warped_slabs(args):
+    """The 4096 x 4096 warped step in row slabs over the ranks (strong scaling)."""
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import paper_1711_09272_gb300 as P  # noqa: F401
+    from paper_1711_09272_gb300.slab import DistExchange, LocalExchange, SlabStepper
+    spec, U = W.warped_step(4096, 4096)
+    ex = DistExchange(torch, device=f"cuda:{local}") if world > 1 else LocalExchange()
+    st = SlabStepper(spec, world, [rank], ex, precision=32, device=local, overlap=True)
+    st.set_state(U)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        st.step(0.5)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    h = st.handles[rank]
+    l0 = h.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        st.step(0.5, nsteps=args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = reduce_max(ev0.elapsed_time(ev1), world)
+    launches = h.launches - l0
+    h.check()
+    value = spec.ncells * 3 * args.steps / (ms * 1e-3) / 1e9
+    j0, j1 = st.slabs[rank][1]
+    if rank == 0:
+        peak, peak_kind = peaks()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "warped step 4096x4096 FP32 (MUSCL van Leer, solid block, walls/inflow/"
+                                       "outflow) in %d row slabs, one per GPU; ghost rows over NCCL in device "
+                                       "memory, overlapped with each slab's interior" % world,
+                           "rows_per_slab": j1 - j0, "cells": spec.ncells,
+                           "exchange_bytes_per_stage_per_side": 2 * 4 * 4 * spec.ni},
+                "roofline": {"bound": "hbm", "achieved": value * (128.0 / 3 + 8), "peak": peak, "unit": "GB/s",
+                             "frac": value * (128.0 / 3 + 8) / (peak * world), "traffic": None,
+                             "peak_kind": peak_kind, "bytes_per_cell_stage": 128.0 / 3 + 8},
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    st.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _spawned_rank(local, n, port, argv):
+    """One rank started by bench.py itself (no torchrun): the environment torchrun would set."""
+    os.environ.update(RANK=str(local), LOCAL_RANK=str(local), WORLD_SIZE=str(n), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    sys.argv = [sys.argv[0]] + argv
+    rc = main()
+    if rc:
+        raise SystemExit(rc)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,9 +632,33 @@ def main():
                                        "precision_comparison"],
                     help="run one side measurement alone and print its JSON (profiling runs)")
     ap.add_argument("--n3", type=int, default=256, help="cells per side of the 3D side measurement")
+    ap.add_argument("--workload", default="batch", choices=["batch", "warped-slabs"],
+                    help="batch: the 512-grid benchmark (weak scaling); warped-slabs: the 4096^2 warped step in "
+                         "row slabs over the GPUs (strong scaling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    env_world = os.environ.get("WORLD_SIZE")
+    if env_world is not None and int(env_world) != args.gpus:
+        print(f"bench.py: WORLD_SIZE={env_world} but --gpus {args.gpus}", file=sys.stderr)
+        return 2
+    if env_world is None and args.gpus > 1:
+        # no launcher: start one rank per GPU here (rank 0 prints the line)
+        import socket
+
+        import torch
+        import torch.multiprocessing as mp
+        if torch.cuda.device_count() < args.gpus:
+            print(f"bench.py: --gpus {args.gpus} but {torch.cuda.device_count()} GPU(s) visible", file=sys.stderr)
+            return 2
+        sk = socket.socket()
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+        sk.close()
+        mp.spawn(_spawned_rank, args=(args.gpus, port, sys.argv[1:]), nprocs=args.gpus, join=True)
+        return 0
+    if args.workload == "warped-slabs" and args.impl == "ours":
+        return run_warped_slabs(args)
     if args.only:
         import torch
         import paper_1711_09272_gb300 as P

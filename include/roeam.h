@@ -111,7 +111,8 @@ typedef struct {
  *              period shift, bit for bit after the subtraction of the reference grid, so
  *              that both sides of the seam see the same face.
  *   solid      host uint8 mask [nj][ni] (1 = solid wall cell, never updated) or NULL.
- *              Solid cells may not be combined with PERIODIC in the same direction. */
+ *              Solid cells may not be combined with PERIODIC in the same direction. A grid
+ *              with an EXCHANGE side takes the mask rows beyond it from roeam_set_halo_solid. */
 typedef struct {
     int ni, nj;
     int bc[4];
@@ -183,6 +184,14 @@ roeam_status roeam_math_check(int device, int n, const double *x, double *out);
  * CFL / max over all slabs of roeam_max_rate. */
 roeam_status roeam_rk_stage(roeam_grid *g, int stage, double dt);
 
+/* The same stage in two launches, so that a slab's ghost-row exchange can overlap its interior:
+ * part ROEAM_PART_INTERIOR updates every cell whose stencil stays inside the grid (all but the
+ * 1 (first order) or 2 (MUSCL) rows next to each EXCHANGE side), part ROEAM_PART_EDGES the rest;
+ * the caller sets the ghost rows (roeam_set_halo) after the first and before the second. Called
+ * in that order, the two parts give the same bits as ROEAM_PART_ALL (= roeam_rk_stage). */
+enum { ROEAM_PART_ALL = 0, ROEAM_PART_INTERIOR = 1, ROEAM_PART_EDGES = 2 };
+roeam_status roeam_rk_stage_part(roeam_grid *g, int stage, double dt, int part);
+
 /* Per-grid largest signal-speed rate sum_dir (|U| + max(c, c~/theta))|S_dir| / V of the current
  * state (rate_out: `count` doubles); CFL / rate is the grid's time step. Synchronises and reports
  * pending device errors. */
@@ -202,6 +211,21 @@ roeam_status roeam_edge_rows(roeam_grid *g, int grid_idx, int side, int stage, v
  * with an EXCHANGE side keeps these rows in its own state planes; they start at zero, so each
  * must be set before the stage that reads it. */
 roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, const void *src);
+
+/* Static ghost rows of a grid with an EXCHANGE side whose neighbouring slab has solid cells or
+ * curvilinear geometry (set once, after roeam_create_grid; they do not change from step to step).
+ *   roeam_set_halo_solid: the solid-mask rows beyond side `side` (2 = S: rows j = -2, -1; 3 = N:
+ *     rows nj, nj+1), host uint8 [2][ni], j increasing. The grid must have a solid mask (pass an
+ *     all-zero one if its own cells are all fluid). Without it the ghost rows are fluid.
+ *   roeam_set_halo_vertices: the vertex rows beyond side `side` (2 = S: J = -2, -1; 3 = N:
+ *     J = nj+1, nj+2), host float64 [2][ni+1] each, J increasing, in the coordinates of the
+ *     grid's own xv, yv (the library stores them relative to the reference grid x = I dx,
+ *     y = J dy like the others). Curvilinear handles only. Without it the ghost vertices sit on
+ *     the reference grid. They give the normals of the faces beyond the side (mirror images of
+ *     solid reconstruction-stencil cells, wall ghost cells of the W/E sides in the ghost rows).
+ * Both copy synchronously and return ROEAM_E_ARG for a side that is not EXCHANGE. */
+roeam_status roeam_set_halo_solid(roeam_grid *g, int grid_idx, int side, const uint8_t *rows);
+roeam_status roeam_set_halo_vertices(roeam_grid *g, int grid_idx, int side, const double *xv, const double *yv);
 
 /* The host-resident form of a step: loads every grid from cons_in (host float64, the layout of
  * roeam_set_state with grid_idx = -1), advances nsteps SSP-RK3 steps as roeam_rk_step does, and

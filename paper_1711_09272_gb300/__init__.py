@@ -12,4 +12,6 @@ from .roeam import (Batch, RoeamError, load_library, make_desc, roeam_cell_count
                     Batch3, make_desc3, roeam3_create_grid, roeam3_destroy_grid, roeam3_set_state, roeam3_get_state,
                     roeam3_flux_residual, roeam3_rk_step, roeam3_conserved_totals, roeam3_check, roeam3_launch_count,
                     roeam_rk_stage, roeam_max_rate, roeam_edge_rows, roeam_set_halo, roeam_math_check,
-                    roeam_step_host, roeam_set_state_device, roeam_get_state_device)
+                    roeam_step_host, roeam_set_state_device, roeam_get_state_device, roeam_rk_stage_part,
+                    roeam_set_halo_solid, roeam_set_halo_vertices, ROEAM_PART_ALL, ROEAM_PART_INTERIOR,
+                    ROEAM_PART_EDGES)

@@ -84,6 +84,9 @@ struct roeam_grid {
     void *d_coef = nullptr;                              // GridCoef<T>[count]
     int4 *d_units_grid = nullptr;   // work units grouped by grid (per-grid launches)
     int4 *d_units_all = nullptr;    // the same units ordered by decreasing size (whole-batch launches)
+    int4 *d_units_part = nullptr;   // interior units (by decreasing size), then the EXCHANGE edge units
+    int part_split = 0;             // first edge unit in d_units_part
+    int part_next = 0;              // 1: the interior part of stage stage_next ran, its edges are due
     int units_cap = 0;
     void *U = nullptr, *A = nullptr, *B = nullptr;      // U^n (in place), stage buffers
     void *vdx = nullptr, *vdy = nullptr;
@@ -135,37 +138,96 @@ roeam_status setup_tiles(roeam_grid *g, int cfg)
         if (units >= warps || ty <= 4) break;
         ty = std::max(4, ty / 2);
     }
-    std::vector<int4> ug;
+    // A single grid has units of one size, so a launch takes ceil(units / warps) rounds of them:
+    // its segment count is raised by up to a quarter where that fills the last round better
+    // (the 4096^2 warped step: 147 x 128 units over 1824 warps fill their eleventh round to 32 %,
+    // 147 x 124 units fill ten rounds to 99.9 %).
+    int single_nty = 0;
+    if (g->count == 1) {
+        const GridDev &G = g->hg[0];
+        const long long ntx = (G.ni + width - 1) / width;
+        const int nty0 = (G.nj + ty - 1) / ty;
+        double best = -1.0;
+        for (int n = std::max(1, nty0 - nty0 / 8); n <= nty0 + nty0 / 4 && n <= G.nj; ++n) {
+            const long long units = ntx * n;
+            const long long rounds = (units + warps - 1) / warps;
+            // useful fraction of the rounds, less the warm-up rows each extra segment re-reads
+            const double eff = (double)units / (double)(rounds * warps) * (1.0 - (double)(H + 1) * n / (2.0 * G.nj));
+            if (eff > best + 1e-9) { best = eff; single_nty = n; }
+        }
+    }
+    // Rows next to an EXCHANGE side (H of them) read its ghost rows; they form segments of their
+    // own, so that a slab can run its interior while its ghost rows are on their way
+    // (roeam_rk_stage_part). Other grids are all interior.
+    std::vector<int4> ug, edges_all;
     g->h_tile_base.assign(g->count + 1, 0);
     for (int k = 0; k < g->count; ++k) {
         GridDev &G = g->hg[k];
+        const bool exS = G.bc[2] == ROEAM_BC_EXCHANGE, exN = G.bc[3] == ROEAM_BC_EXCHANGE;
+        int lo = exS ? H : 0, hi = exN ? G.nj - H : G.nj;
+        if (hi - lo < 1) lo = hi = 0;   // (a slab too thin for an interior: one edge segment)
+        const int nin = hi - lo;
         G.ntx = (G.ni + width - 1) / width;
-        G.nty = (G.nj + ty - 1) / ty;
-        G.ntiles = G.ntx * G.nty;
+        int nseg = nin > 0 ? (single_nty > 0 ? single_nty : (nin + ty - 1) / ty) : 0;
+        nseg = std::min(nseg, std::max(nin, 0));
         G.tile_base = (int)ug.size();
         g->h_tile_base[k] = G.tile_base;
-        for (int sg = 0; sg < G.nty; ++sg) {
-            const int j0 = (int)((long long)sg * G.nj / G.nty), j1 = (int)((long long)(sg + 1) * G.nj / G.nty);
+        for (int sg = 0; sg < nseg; ++sg) {
+            const int j0 = lo + (int)((long long)sg * nin / nseg), j1 = lo + (int)((long long)(sg + 1) * nin / nseg);
             for (int st = 0; st < G.ntx; ++st) ug.push_back(make_int4(k, st * width - H, j0, j1));
         }
+        std::vector<std::pair<int, int>> eseg;
+        if (nin == 0) eseg.emplace_back(0, G.nj);
+        else {
+            if (lo > 0) eseg.emplace_back(0, lo);
+            if (hi < G.nj) eseg.emplace_back(hi, G.nj);
+        }
+        for (const auto &e : eseg)
+            for (int st = 0; st < G.ntx; ++st) {
+                ug.push_back(make_int4(k, st * width - H, e.first, e.second));
+                edges_all.push_back(ug.back());
+            }
+        G.nty = nseg + (int)eseg.size();
+        G.ntiles = (int)ug.size() - G.tile_base;
     }
     const int base = (int)ug.size();
     g->h_tile_base[g->count] = base;
     g->total_tiles = base;
+    auto taller = [](const int4 &a, const int4 &b) { return (a.w - a.z) > (b.w - b.z); };
     std::vector<int4> ua(ug);
-    std::stable_sort(ua.begin(), ua.end(), [](const int4 &a, const int4 &b) { return (a.w - a.z) > (b.w - b.z); });
+    std::stable_sort(ua.begin(), ua.end(), taller);
+    // interior units (every unit that is not an edge unit) by height, then the edge units
+    std::vector<int4> up;
+    {
+        std::vector<int4> interior;
+        size_t e = 0;
+        for (int k = 0; k < g->count; ++k)
+            for (int t = g->h_tile_base[k]; t < g->h_tile_base[k + 1]; ++t) {
+                const int4 q = ug[t];
+                if (e < edges_all.size() && q.x == edges_all[e].x && q.y == edges_all[e].y && q.z == edges_all[e].z &&
+                    q.w == edges_all[e].w) ++e;
+                else interior.push_back(q);
+            }
+        std::stable_sort(interior.begin(), interior.end(), taller);
+        up = interior;
+        g->part_split = (int)up.size();
+        up.insert(up.end(), edges_all.begin(), edges_all.end());
+    }
     if (base > g->units_cap) {
         CUDA_TRY(cudaStreamSynchronize(g->stream));
         cudaFree(g->d_units_grid);
         cudaFree(g->d_units_all);
-        g->d_units_grid = g->d_units_all = nullptr;
+        cudaFree(g->d_units_part);
+        g->d_units_grid = g->d_units_all = g->d_units_part = nullptr;
         CUDA_TRY(cudaMalloc(&g->d_units_grid, sizeof(int4) * base));
         CUDA_TRY(cudaMalloc(&g->d_units_all, sizeof(int4) * base));
+        CUDA_TRY(cudaMalloc(&g->d_units_part, sizeof(int4) * base));
         g->units_cap = base;
     }
     CUDA_TRY(cudaMemcpyAsync(g->d_grids, g->hg.data(), sizeof(GridDev) * g->count, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaMemcpyAsync(g->d_units_grid, ug.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaMemcpyAsync(g->d_units_all, ua.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(g->d_units_part, up.data(), sizeof(int4) * base, cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     g->nblocks = std::max(1, occ * g->num_sms);
     g->eff_ty = ty;
@@ -566,8 +628,6 @@ roeam_status validate(int count, const roeam_grid_desc *d)
             if (q.bc[s] < 0 || q.bc[s] > 4) return fail(ROEAM_E_ARG, "grid %d: bad boundary type on side %d", k, s);
         if (q.bc[0] == ROEAM_BC_EXCHANGE || q.bc[1] == ROEAM_BC_EXCHANGE)
             return fail(ROEAM_E_ARG, "grid %d: EXCHANGE is for the S and N sides (row slabs)", k);
-        if (q.solid && (q.bc[2] == ROEAM_BC_EXCHANGE || q.bc[3] == ROEAM_BC_EXCHANGE))
-            return fail(ROEAM_E_ARG, "grid %d: solid cells cannot be combined with EXCHANGE sides", k);
         if ((q.bc[0] == ROEAM_BC_PERIODIC) != (q.bc[1] == ROEAM_BC_PERIODIC) ||
             (q.bc[2] == ROEAM_BC_PERIODIC) != (q.bc[3] == ROEAM_BC_PERIODIC))
             return fail(ROEAM_E_ARG, "grid %d: PERIODIC must be set on both sides of a direction", k);
@@ -585,7 +645,7 @@ roeam_status validate(int count, const roeam_grid_desc *d)
 namespace {
 
 template <typename T>
-roeam_status do_stage(roeam_grid *g, int stage, double dt)
+roeam_status do_stage(roeam_grid *g, int stage, double dt, int part = 0)
 {
     const int par = (int)(g->step & 1);
     unsigned long long *rd = g->rate + (size_t)par * g->count;
@@ -600,8 +660,19 @@ roeam_status do_stage(roeam_grid *g, int stage, double dt)
     if (stage == 0) { a.src = U; a.un = U; a.dst = A; a.alpha = T(0); a.beta = T(1); a.rate_zero = wr; }
     else if (stage == 1) { a.src = A; a.un = U; a.dst = B; a.alpha = T(0.75); a.beta = T(0.25); }
     else { a.src = B; a.un = U; a.dst = U; a.alpha = T(1.0 / 3.0); a.beta = T(2.0 / 3.0); a.rate_wr = wr; a.want_rate = 1; }
-    CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, g->stream));
-    g->launches += 1;
+    if (part != 0) {
+        // interior units (part 1) or the units next to EXCHANGE sides (part 2); the next step's
+        // rate slots are reset here rather than by a kernel, which either part may lack
+        if (stage == 0 && part == 1) CUDA_TRY(cudaMemsetAsync(wr, 0, sizeof(unsigned long long) * g->count, g->stream));
+        a.rate_zero = nullptr;
+        a.units = g->d_units_part;
+        a.tile_lo = part == 1 ? 0 : g->part_split;
+        a.tile_hi = part == 1 ? g->part_split : g->total_tiles;
+    }
+    if (a.tile_hi > a.tile_lo) {
+        CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, g->stream));
+        g->launches += 1;
+    }
     return ROEAM_OK;
 }
 
@@ -724,16 +795,18 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
         G.off = off + (exch ? 2ll * G.pitch : 0);
         off += 4 * G.plane;
         if (g->curv) {
+            // (an EXCHANGE grid also keeps two ghost vertex rows below and above, roeam_set_halo_vertices)
             G.vpitch = (int)round_up(q.ni + 1, 32);
-            G.voff = voff;
-            voff += (long long)(q.nj + 1) * G.vpitch;
+            G.voff = voff + (exch ? 2ll * G.vpitch : 0);
+            voff += (long long)(q.nj + 1 + (exch ? 4 : 0)) * G.vpitch;
         } else {
             G.voff = -1;
         }
         long long nf = (long long)q.ni * q.nj;
         if (q.solid) {
-            G.soff = soff;
-            soff += round_up((long long)q.ni * q.nj, 256);
+            // (an EXCHANGE grid also keeps two ghost mask rows below and above, roeam_set_halo_solid)
+            G.soff = soff + (exch ? 2ll * q.ni : 0);
+            soff += round_up((long long)q.ni * (q.nj + (exch ? 4 : 0)), 256);
             any_solid = true;
             for (long long c = 0; c < (long long)q.ni * q.nj; ++c) nf -= q.solid[c] ? 1 : 0;
         } else {
@@ -846,6 +919,7 @@ void roeam_destroy_grid(roeam_grid *g)
     cudaFree(g->d_coef);
     cudaFree(g->d_units_grid);
     cudaFree(g->d_units_all);
+    cudaFree(g->d_units_part);
     cudaFree(g->U);
     cudaFree(g->A);
     cudaFree(g->B);
@@ -948,7 +1022,7 @@ roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nstep
     if (!std::isfinite(cfl) || !std::isfinite(dt_fixed)) return fail(ROEAM_E_ARG, "cfl and dt_fixed must be finite");
     for (int k = 0; k < g->count; ++k)
         if (!g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
-    if (g->stage_next != 0) return fail(ROEAM_E_STATE, "a step run by roeam_rk_stage is unfinished");
+    if (g->stage_next != 0 || g->part_next != 0) return fail(ROEAM_E_STATE, "a step run by roeam_rk_stage is unfinished");
     CUDA_TRY(cudaSetDevice(g->device));
     const long long step0 = g->step;
     roeam_status st = g->precision == 32 ? rk_steps<float>(g, cfl, dt_fixed, nsteps)
@@ -1164,12 +1238,30 @@ roeam_status roeam_rk_stage(roeam_grid *g, int stage, double dt)
     if (!g) return fail(ROEAM_E_ARG, "null handle");
     if (stage < 0 || stage > 2) return fail(ROEAM_E_ARG, "stage must be 0, 1 or 2");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ROEAM_E_ARG, "dt must be finite and > 0");
+    return roeam_rk_stage_part(g, stage, dt, ROEAM_PART_ALL);
+}
+
+roeam_status roeam_rk_stage_part(roeam_grid *g, int stage, double dt, int part)
+{
+    if (!g) return fail(ROEAM_E_ARG, "null handle");
+    if (stage < 0 || stage > 2) return fail(ROEAM_E_ARG, "stage must be 0, 1 or 2");
+    if (part < ROEAM_PART_ALL || part > ROEAM_PART_EDGES) return fail(ROEAM_E_ARG, "part must be 0, 1 or 2");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ROEAM_E_ARG, "dt must be finite and > 0");
     if (stage != g->stage_next) return fail(ROEAM_E_STATE, "stage %d expected, %d given", g->stage_next, stage);
+    if (g->part_next == 1 && part != ROEAM_PART_EDGES)
+        return fail(ROEAM_E_STATE, "the edge part of stage %d is due", stage);
+    if (g->part_next == 0 && part == ROEAM_PART_EDGES)
+        return fail(ROEAM_E_STATE, "the interior part of stage %d comes first", stage);
     for (int k = 0; k < g->count; ++k)
         if (!g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
     CUDA_TRY(cudaSetDevice(g->device));
-    roeam_status st = g->precision == 32 ? do_stage<float>(g, stage, dt) : do_stage<double>(g, stage, dt);
+    roeam_status st = g->precision == 32 ? do_stage<float>(g, stage, dt, part) : do_stage<double>(g, stage, dt, part);
     if (st != ROEAM_OK) return st;
+    if (part == ROEAM_PART_INTERIOR) {
+        g->part_next = 1;
+        return ROEAM_OK;
+    }
+    g->part_next = 0;
     g->stage_next = (stage + 1) % 3;
     if (stage == 2) g->step += 1;
     return ROEAM_OK;
@@ -1223,6 +1315,60 @@ roeam_status roeam_set_halo(roeam_grid *g, int grid_idx, int side, int stage, co
         CUDA_TRY(cudaStreamSynchronize(g->stream));
     }
     return ROEAM_OK;
+}
+
+roeam_status roeam_set_halo_solid(roeam_grid *g, int grid_idx, int side, const uint8_t *rows)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (grid_idx < 0) return fail(ROEAM_E_ARG, "ghost rows need one grid (grid_idx >= 0)");
+    if (side != 2 && side != 3) return fail(ROEAM_E_ARG, "side must be 2 (S) or 3 (N)");
+    const GridDev &G = g->hg[grid_idx];
+    if (G.bc[side] != ROEAM_BC_EXCHANGE) return fail(ROEAM_E_ARG, "side %d of grid %d is not EXCHANGE", side, grid_idx);
+    if (G.soff < 0) return fail(ROEAM_E_ARG, "grid %d has no solid mask (give it one, all zeros if need be)", grid_idx);
+    if (!rows) return fail(ROEAM_E_ARG, "rows must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    std::vector<uint8_t> h(2 * (size_t)G.ni);
+    for (size_t c = 0; c < h.size(); ++c) h[c] = rows[c] ? 1 : 0;
+    const long long r0 = side == 2 ? -2 : G.nj;
+    CUDA_TRY(cudaMemcpyAsync(g->solid + G.soff + r0 * G.ni, h.data(), h.size(), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return ROEAM_OK;
+}
+
+extern "C++" {
+template <typename T>
+static roeam_status set_halo_vertices(roeam_grid *g, const GridDev &G, int side, const double *xv, const double *yv)
+{
+    std::vector<T> hx(2 * (size_t)G.vpitch, T(0)), hy(2 * (size_t)G.vpitch, T(0));
+    const int J0 = side == 2 ? -2 : G.nj + 1;
+    for (int r = 0; r < 2; ++r)
+        for (int I = 0; I <= G.ni; ++I) {
+            const size_t s = (size_t)r * (G.ni + 1) + I;
+            hx[(size_t)r * G.vpitch + I] = T(xv[s] - I * G.dx);
+            hy[(size_t)r * G.vpitch + I] = T(yv[s] - (J0 + r) * G.dy);
+        }
+    const size_t at = (size_t)(G.voff + (long long)J0 * G.vpitch);
+    CUDA_TRY(cudaMemcpyAsync((T *)g->vdx + at, hx.data(), sizeof(T) * hx.size(), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaMemcpyAsync((T *)g->vdy + at, hy.data(), sizeof(T) * hy.size(), cudaMemcpyHostToDevice, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return ROEAM_OK;
+}
+}  // extern "C++"
+
+roeam_status roeam_set_halo_vertices(roeam_grid *g, int grid_idx, int side, const double *xv, const double *yv)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (grid_idx < 0) return fail(ROEAM_E_ARG, "ghost rows need one grid (grid_idx >= 0)");
+    if (side != 2 && side != 3) return fail(ROEAM_E_ARG, "side must be 2 (S) or 3 (N)");
+    const GridDev &G = g->hg[grid_idx];
+    if (G.bc[side] != ROEAM_BC_EXCHANGE) return fail(ROEAM_E_ARG, "side %d of grid %d is not EXCHANGE", side, grid_idx);
+    if (!g->curv) return fail(ROEAM_E_ARG, "the handle's grids are Cartesian");
+    if (!xv || !yv) return fail(ROEAM_E_ARG, "xv and yv must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    return g->precision == 32 ? set_halo_vertices<float>(g, G, side, xv, yv)
+                              : set_halo_vertices<double>(g, G, side, xv, yv);
 }
 
 roeam_status roeam_math_check(int device, int n, const double *x, double *out)

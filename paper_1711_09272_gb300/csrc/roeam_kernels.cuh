@@ -661,7 +661,7 @@ __device__ __forceinline__ void issue_cell(const GridRegs<T> &R, int isrc, int k
         q.raw[1] = ld_row<KEEP>(R.src + x + R.plane);
         q.raw[2] = ld_row<KEEP>(R.src + x + 2 * R.plane);
         q.raw[3] = ld_row<KEEP>(R.src + x + 3 * R.plane);
-        // (grids with solid cells have no EXCHANGE side, so jsrc is a grid row here)
+        // (jsrc is a grid row, or an EXCHANGE ghost row, whose mask rows the grid also keeps)
         if constexpr (WALLS)
             if (R.solid) q.solid = __ldg(R.solid + q.jsrc * R.ni + isrc);
     }
@@ -703,7 +703,9 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
         if (kx == 1) {
             T nx = T(1), ny = T(0);
             if constexpr (CURV) {
-                const int b = clampi(j, 0, R.nj - 1) * R.vpitch + (i < 0 ? 0 : R.ni);
+                // (the W/E boundary face of row j, ghost rows of EXCHANGE sides included)
+                const int b = clampi(j, R.bcS == BC_EXCHANGE ? -2 : 0, R.bcN == BC_EXCHANGE ? R.nj + 1 : R.nj - 1) *
+                                  R.vpitch + (i < 0 ? 0 : R.ni);
                 const T sx = K.dy + (R.vdy[b + R.vpitch] - R.vdy[b]), sy = -(R.vdx[b + R.vpitch] - R.vdx[b]);
                 const T l = rsq(vfma(sx, sx, sy * sy));
                 nx = sx * l; ny = sy * l;
@@ -818,9 +820,11 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         T Px[NW], Py[NW - 1];
         T vX[NV], vY[NV];
         Pending<T> pend;
+        // vertex rows 0..nj, and the two ghost vertex rows beyond an EXCHANGE side
+        const int vjlo = R.bcS == BC_EXCHANGE ? -2 : 0, vjhi = R.bcN == BC_EXCHANGE ? nj + 2 : nj;
         auto vload = [&](int J, T &x, T &y) {
             if constexpr (CURV) {
-                const int b = clampi(J, 0, nj) * R.vpitch + clampi(i, 0, ni);
+                const int b = clampi(J, vjlo, vjhi) * R.vpitch + clampi(i, 0, ni);
                 x = __ldg(R.vdx + b); y = __ldg(R.vdy + b);
             } else { x = y = T(0); }
         };

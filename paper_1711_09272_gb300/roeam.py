@@ -27,8 +27,8 @@ EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_
            "roeam_rk_step", "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_launch_count",
            "roeam_cell_count", "roeam_last_error", "roeam_version", "roeam_tile_config_count",
            "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc",
-           "roeam_rk_stage", "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check",
-           "roeam_step_host",
+           "roeam_rk_stage", "roeam_rk_stage_part", "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo",
+           "roeam_set_halo_solid", "roeam_set_halo_vertices", "roeam_math_check", "roeam_step_host",
            "roeam3_create_grid", "roeam3_destroy_grid", "roeam3_set_state", "roeam3_get_state",
            "roeam3_flux_residual", "roeam3_rk_step", "roeam3_conserved_totals", "roeam3_check",
            "roeam3_launch_count"]
@@ -96,6 +96,9 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_autotune.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
     lib.roeam_flux_residual_noalloc.argtypes = [vp, C.c_int, vp]
     lib.roeam_rk_stage.argtypes = [vp, C.c_int, C.c_double]
+    lib.roeam_rk_stage_part.argtypes = [vp, C.c_int, C.c_double, C.c_int]
+    lib.roeam_set_halo_solid.argtypes = [vp, C.c_int, C.c_int, vp]
+    lib.roeam_set_halo_vertices.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.roeam_math_check.argtypes = [C.c_int, C.c_int, dp, dp]
     lib.roeam_step_host.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp, vp]
     lib.roeam_max_rate.argtypes = [vp, dp]
@@ -117,6 +120,7 @@ def load_library(path: str = LIB_PATH):
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
                  "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam_rk_stage",
                  "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check", "roeam_step_host",
+                 "roeam_rk_stage_part", "roeam_set_halo_solid", "roeam_set_halo_vertices",
                  "roeam3_create_grid",
                  "roeam3_set_state", "roeam3_get_state", "roeam3_flux_residual", "roeam3_rk_step",
                  "roeam3_conserved_totals", "roeam3_check"):
@@ -254,6 +258,25 @@ def roeam_math_check(x, device: int = 0) -> np.ndarray:
 
 def roeam_rk_stage(h: int, stage: int, dt: float) -> None:
     _check(load_library().roeam_rk_stage(C.c_void_p(h), stage, dt))
+
+
+ROEAM_PART_ALL, ROEAM_PART_INTERIOR, ROEAM_PART_EDGES = 0, 1, 2
+
+
+def roeam_rk_stage_part(h: int, stage: int, dt: float, part: int) -> None:
+    _check(load_library().roeam_rk_stage_part(C.c_void_p(h), stage, dt, part))
+
+
+def roeam_set_halo_solid(h: int, grid_idx: int, side: int, rows) -> None:
+    rows = np.ascontiguousarray(rows, dtype=np.uint8)
+    _check(load_library().roeam_set_halo_solid(C.c_void_p(h), grid_idx, side, C.c_void_p(rows.ctypes.data)))
+
+
+def roeam_set_halo_vertices(h: int, grid_idx: int, side: int, xv, yv) -> None:
+    xv = np.ascontiguousarray(xv, dtype=np.float64)
+    yv = np.ascontiguousarray(yv, dtype=np.float64)
+    _check(load_library().roeam_set_halo_vertices(C.c_void_p(h), grid_idx, side, C.c_void_p(xv.ctypes.data),
+                                                  C.c_void_p(yv.ctypes.data)))
 
 
 def roeam_max_rate(h: int, count: int) -> np.ndarray:
@@ -394,6 +417,17 @@ class Batch:
     # stage-by-stage stepping of row slabs (EXCHANGE sides; see include/roeam.h)
     def stage(self, stage: int, dt: float):
         roeam_rk_stage(self.handle, stage, dt)
+
+    def stage_part(self, stage: int, dt: float, part: int):
+        roeam_rk_stage_part(self.handle, stage, dt, part)
+
+    def set_halo_solid(self, grid_idx: int, side: int, rows):
+        """Solid-mask rows (2, ni) beyond EXCHANGE side `side` (static)."""
+        roeam_set_halo_solid(self.handle, grid_idx, side, rows)
+
+    def set_halo_vertices(self, grid_idx: int, side: int, xv, yv):
+        """Vertex rows (2, ni + 1) beyond EXCHANGE side `side` (static, curvilinear grids)."""
+        roeam_set_halo_vertices(self.handle, grid_idx, side, xv, yv)
 
     def max_rate(self) -> np.ndarray:
         return roeam_max_rate(self.handle, len(self.specs))

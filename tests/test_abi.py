@@ -66,19 +66,17 @@ def test_create_rejects_bad_arguments_without_gpu_work():
 
 
 def test_exchange_sides_are_validated():
-    """EXCHANGE (row slabs) is accepted on S/N only and not with solid cells."""
+    """EXCHANGE (row slabs) is accepted on S/N only, with or without solid cells."""
     import numpy as np
     import workloads as W
     import paper_1711_09272_gb300 as P
     for bc in ((4, W.OUTFLOW, W.WALL, W.WALL), (W.OUTFLOW, 4, W.WALL, W.WALL)):
-        with pytest.raises(P.RoeamError) as e:
-            P.roeam_create_grid([P.make_desc(W.GridSpec(ni=8, nj=8, bc=bc))])
-        assert "EXCHANGE" in str(e.value)
-    spec = W.GridSpec(ni=8, nj=8, bc=(W.OUTFLOW, W.OUTFLOW, 4, W.WALL))
-    spec.solid = np.zeros((8, 8), np.uint8)
-    with pytest.raises(P.RoeamError) as e:
-        P.roeam_create_grid([P.make_desc(spec)])
-    assert "EXCHANGE" in str(e.value)
+        for solid in (None, np.zeros((8, 8), np.uint8)):
+            spec = W.GridSpec(ni=8, nj=8, bc=bc)
+            spec.solid = solid
+            with pytest.raises(P.RoeamError) as e:
+                P.roeam_create_grid([P.make_desc(spec)])
+            assert "EXCHANGE" in str(e.value)
 
 
 def test_size_limits_are_validated():

@@ -57,3 +57,28 @@ def test_gpu_arm_line():
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 8 * 4 * cells
     c = d["clocks"]
     assert "sm_mhz" in c and "sm_max_mhz" in c and isinstance(c["reasons"], list)
+
+
+def test_gpus_flag_and_world_size_must_agree():
+    """--gpus N and a launcher's WORLD_SIZE must agree, and without a launcher bench.py starts N
+    ranks itself only when N GPUs are visible; a mismatch exits non-zero before any work."""
+    env = dict(os.environ, WORLD_SIZE="2", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, "bench.py", "--gpus", "1", "--steps", "1"], cwd=ROOT, capture_output=True,
+                       text=True, env=env, timeout=300)
+    assert r.returncode != 0 and "WORLD_SIZE" in r.stderr
+    import torch
+    if torch.cuda.device_count() < 64:
+        env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+        r = subprocess.run([sys.executable, "bench.py", "--gpus", "64", "--steps", "1"], cwd=ROOT,
+                           capture_output=True, text=True, env=env, timeout=300)
+        assert r.returncode != 0 and "visible" in r.stderr
+
+
+@pytest.mark.gpu
+def test_warped_slabs_line():
+    """The strong-scaling slab workload on one GPU (one slab, the same stage-part path)."""
+    d = run_bench("--workload", "warped-slabs", "--steps", "4", "--warmup", "3")
+    for k in COMMON + ("roofline", "gpu_launches", "clocks"):
+        assert k in d, k
+    assert d["scaling"] == "strong" and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["config"]["cells"] == 4096 * 4096

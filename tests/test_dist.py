@@ -52,6 +52,10 @@ def test_two_rank_weak_scaling_host_logic():
 # ----------------------------------------------------------------------------- row slabs
 def _slab_case(name):
     import workloads as W
+    if name == "warped_solid":
+        # the Mach-3 step (solid block, walls, inflow, outflow, van Leer) on a small warped grid
+        spec, _ = W.warped_step(24, 20, with_state=False)
+        return spec, W.random_smooth_state(spec, seed=6, mach=2.0, amp=0.2)
     if name == "periodic":
         spec = W.GridSpec(ni=22, nj=17, dx=0.05, dy=0.06, params=W.SchemeParams(m_ref=0.4, recon=2))
     else:
@@ -85,7 +89,7 @@ def _slab_worker(rank, world, port, name, out):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["periodic", "wall_inflow"])
+@pytest.mark.parametrize("name", ["periodic", "wall_inflow", "warped_solid"])
 def test_two_rank_row_slabs_match_the_whole_grid(name):
     """A grid split into two row slabs on two gloo ranks (halo exchange before every stage, a
     max-reduction of the rate per step) advances exactly like the whole grid: the stepper's
@@ -129,3 +133,30 @@ def test_local_three_slabs_match_the_whole_grid():
     Ur, _ = oracle.OracleGrid(spec).step(U, cfl=0.5, nsteps=2)
     got = st.get_state(np.zeros_like(U))
     assert np.max(np.abs(got - Ur).reshape(4, -1).max(axis=1) / np.abs(Ur).reshape(4, -1).max(axis=1)) < 1e-13
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_local_slabs_with_solid_ghost_rows(overlap):
+    """Five slabs of the warped step (20 rows): the slab edges at rows 4 and 8 cut through the
+    solid block's top (rows 0-3), so ghost rows hold solid cells and MUSCL stencils reach into
+    them; the static ghost rows (mask, vertices) and the interior / edge split of every stage
+    reproduce the whole grid."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import numpy as np
+    import oracle
+    from paper_1711_09272_gb300.slab import LocalExchange, SlabStepper, partition
+    from slab_oracle import OracleSlab
+    spec, U = _slab_case("warped_solid")
+    slabs = partition(spec, 5)
+    assert any(np.any(sl[4]["solid"].get(2, np.zeros(1))) for sl in slabs)
+    st = SlabStepper(spec, 5, list(range(5)), LocalExchange(), make_slab=OracleSlab, overlap=overlap)
+    st.set_state(U)
+    dts = [st.step(0.5) for _ in range(2)]
+    got = st.get_state(np.zeros_like(U))
+    g = oracle.OracleGrid(spec)
+    Ur = U.copy()
+    for dt in dts:
+        Ur, _ = g.step(Ur, dt_fixed=dt)
+    scale = np.abs(Ur).reshape(4, -1).max(axis=1)[:, None, None]
+    assert np.max(np.abs(got - Ur) / scale) < 1e-13
