@@ -231,6 +231,43 @@ def precision_comparison(P, torch, n=1024, t_end=1.0):
     return out
 
 
+def oracle_comparison(P):
+    """Part of the CPU-baseline leg (the one place besides the reference arm where the bench runs
+    the oracle): FP32 (and FP64) GPU results against the FP64 oracle: the per-step error relative to the
+    step's increment on the low-Mach Gresho vortex (256 x 256, M = 0.01, MUSCL minmod: the
+    increment is a small fraction of the state there), and the L2 state difference after N
+    steps of independent trajectories from the same state (isentropic vortex 64 x 64, 100
+    steps; Gresho vortex 256 x 256, 100 steps)."""
+    import oracle
+    out = {}
+    spec, U = W.gresho(256, mach=0.01)
+    for prec in (32, 64):
+        with P.Batch([spec], precision=prec) as b:
+            b.set_state(U, 0)
+            U0 = b.get_state(0)
+            b.step(0.5, nsteps=1)
+            Ug = b.get_state(0)
+        Uo, _ = oracle.OracleGrid(spec).step(U0, cfl=0.5)
+        d = np.abs(Ug - Uo).reshape(4, -1).max(axis=1)
+        inc = np.abs(Uo - U0).reshape(4, -1).max(axis=1)
+        scale = np.abs(Uo).reshape(4, -1).max(axis=1)
+        out[f"gresho_256_one_step_fp{prec}"] = {"increment_rel_err": [float(x) for x in d / inc],
+                                               "state_rel_err": [float(x) for x in d / scale],
+                                               "increment_over_state": [float(x) for x in inc / scale]}
+    for name, (spec, U), n, precs in (("vortex_64_100_steps", W.isentropic_vortex(64), 100, (32, 64)),
+                                      ("gresho_256_100_steps", W.gresho(256, mach=0.01), 100, (32,))):
+        for prec in precs:
+            with P.Batch([spec], precision=prec) as b:
+                b.set_state(U, 0)
+                U0 = b.get_state(0)
+                b.step(0.5, nsteps=n)
+                Ug = b.get_state(0)
+            Uo, _ = oracle.OracleGrid(spec).step(U0, cfl=0.5, nsteps=n)
+            l2 = np.sqrt(((Ug - Uo) ** 2).reshape(4, -1).sum(axis=1) / (Uo ** 2).reshape(4, -1).sum(axis=1))
+            out[f"{name}_fp{prec}_l2_vs_oracle"] = [float(x) for x in l2]
+    return out
+
+
 def warped_step_speed(P, torch, steps=20):
     """The large curvilinear FP32 workload (4096 x 4096 warped grid, Mach-3 step, MUSCL van
     Leer, solid block): device speed and its HBM fraction (50.67 algorithmic B/cell/stage)."""
@@ -506,9 +543,12 @@ def run_ours(args):
     line = None
     if rank == 0:
         cpu_v, cpu_sample, cpu_all = (None, None, None)
+        vs_oracle = None
         if world == 1 and not args.no_cpu:
             cpu_v, cpu_sample = cpu_baseline(specs, states, steps=1, budget_s=args.cpu_budget)
             cpu_all = cpu_baseline_all_cores(rank_seed(rank), args.grids, args.cpu_budget)
+            if not args.no_extra:
+                vs_oracle = oracle_comparison(P)
         traffic = measured_traffic(ncells)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -529,7 +569,8 @@ def run_ours(args):
                 "value": cpu_all[0], "unit": UNIT, "cores": cpu_all[1], "kind": "oracle",
                 "sample": f"FP64 C oracle as independent processes, one per core, each stepping its share of "
                           f"the same batch's grids for {args.cpu_budget:.0f} s",
-                "single_core": {"value": cpu_v, "cores": 1, "sample": cpu_sample}},
+                "single_core": {"value": cpu_v, "cores": 1, "sample": cpu_sample},
+                "gpu_vs_oracle": vs_oracle},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),

@@ -45,7 +45,9 @@ typedef enum {
     ROEAM_E_NONPOSITIVE = 4,  /* density or pressure <= 0 after a step */
     ROEAM_E_NONFINITE = 5,    /* NaN or Inf in the state after a step */
     ROEAM_E_TIMEOUT = 6,      /* a bounded device wait gave up */
-    ROEAM_E_STATE = 7         /* call not valid in the handle's current state */
+    ROEAM_E_STATE = 7,        /* call not valid in the handle's current state */
+    ROEAM_E_BOUNDS = 8        /* a kernel index left its buffer (only libraries built with
+                                 ROEAM_DEBUG check; the access was skipped, nothing trapped) */
 } roeam_status;
 
 enum { ROEAM_BC_PERIODIC = 0, ROEAM_BC_WALL = 1, ROEAM_BC_INFLOW = 2, ROEAM_BC_OUTFLOW = 3, ROEAM_BC_EXCHANGE = 4 };

@@ -34,25 +34,35 @@ def nvcc() -> str:
     return exe
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+DEBUG_DIR = os.path.join(HERE, "_build_debug")
+
+
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", f) for f in
                                                               os.listdir(os.path.join(ROOT, "include"))] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Builds libroeam.so if missing or older than its sources; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Builds libroeam.so if missing or older than its sources; returns its path. debug=True
+    builds the bounds-checked library (-DROEAM_DEBUG: every state, mask and vertex access of the
+    2D stage kernels is checked and reported as ROEAM_E_BOUNDS instead of faulting) into
+    _build_debug/."""
+    out_dir = DEBUG_DIR if debug else OUT_DIR
+    lib_path = os.path.join(out_dir, "libroeam.so")
+    if not force and not _stale(lib_path):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
-    objs = [os.path.join(OUT_DIR, os.path.splitext(s)[0] + ".o") for s in SOURCES]
+    objs = [os.path.join(out_dir, os.path.splitext(s)[0] + ".o") for s in SOURCES]
 
     def compile_one(k):
         extra = ["-fmad=false"] if SOURCES[k] in EXACT_FMA else []
+        if debug:
+            extra.append("-DROEAM_DEBUG")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, SOURCES[k]), "-o", objs[k]]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -63,16 +73,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         logs = list(ex.map(compile_one, range(len(SOURCES))))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     if verbose:
         print("\n".join(logs))
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -324,6 +324,9 @@ StageArgs<T> base_args(roeam_grid *g)
     a.solid = g->solid;
     a.status = g->status;
     a.work = g->eff_dyn ? g->work : nullptr;
+    a.n_state = a.n_dst = g->total_elems;
+    a.n_vert = g->total_vert;
+    a.n_solid = g->total_solid;
     return a;
 }
 
@@ -429,6 +432,7 @@ roeam_status read_status(roeam_grid *g)
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     if (st) {
         CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(unsigned), g->stream));
+        if (st & ST_BOUNDS) return fail(ROEAM_E_BOUNDS, "a kernel index left its buffer (bounds-checked build)");
         if (st & ST_NONFINITE) return fail(ROEAM_E_NONFINITE, "non-finite state after a step");
         return fail(ROEAM_E_NONPOSITIVE, "non-positive density or pressure after a step");
     }
@@ -1522,6 +1526,7 @@ roeam_status do_residual_noalloc(roeam_grid *g, int idx, double *out)
     a.un = (const T *)g->U;
     a.dst = region_t;
     a.dst_shift = G.off;
+    a.n_dst = 4 * G.plane;
     a.units = g->d_units_grid;
     a.tile_lo = g->h_tile_base[idx];
     a.tile_hi = g->h_tile_base[idx + 1];

@@ -12,6 +12,7 @@ constexpr int BC_PERIODIC = 0, BC_WALL = 1, BC_INFLOW = 2, BC_OUTFLOW = 3, BC_EX
 
 // Status bits raised by kernels (read back by the host at synchronising calls).
 constexpr unsigned ST_NONPOSITIVE = 1u, ST_NONFINITE = 2u;
+constexpr unsigned ST_BOUNDS = 4u;   // an index outside its buffer (bounds-checked debug builds only)
 
 // Per-grid descriptor, resident in device memory, read-only in kernels.
 struct GridDev {
@@ -74,6 +75,9 @@ struct StageArgs {
     // each warp's first, work[1] the warps that have finished; the last warp to finish resets
     // both, so that the next launch on the handle's stream starts from zero.
     unsigned *work;
+    // buffer sizes (elements of each state buffer and of dst, of each vertex plane buffer; bytes of
+    // the solid masks), read by the bounds checks of debug builds
+    long long n_state, n_dst, n_vert, n_solid;
 };
 
 // Work-unit shapes of the stage kernel: a warp sweeps a strip tx = 32 lanes wide (2H of

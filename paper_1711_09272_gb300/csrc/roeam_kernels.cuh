@@ -620,6 +620,31 @@ __device__ __forceinline__ void faces_packed(const Face<float> &fx, const Face<f
 
 // ------------------------------------------------------------------ the fused stage kernel
 // Per-grid values a warp keeps in registers while it sweeps a strip.
+// Bounds-checked debug builds (-DROEAM_DEBUG): every state, mask and vertex access of the
+// stage kernel is checked against its whole buffer; an access outside it sets ST_BOUNDS in the
+// status word (reported as ROEAM_E_BOUNDS) and reads zeros or is skipped instead of faulting.
+#ifdef ROEAM_DEBUG
+__device__ __align__(16) unsigned char dbg_sink[16];
+struct DbgBufs {
+    const unsigned char *lo[6];   // src, un, dst, vdx, vdy, solid
+    unsigned long long bytes[6];
+    unsigned *status;
+};
+template <typename P> __device__ __forceinline__ bool dbg_ok(const DbgBufs &d, int buf, P *p)
+{
+    const unsigned char *q = (const unsigned char *)p;
+    if (d.lo[buf] && q >= d.lo[buf] && q + sizeof(P) <= d.lo[buf] + d.bytes[buf]) return true;
+    atomicOr(d.status, ST_BOUNDS);
+    return false;
+}
+#define DBG_LD(R, buf, p) (dbg_ok((R).dbg, (buf), (p)) ? (p) : (decltype(p))dbg_sink)
+#define DBG_ST(R, buf, p) dbg_ok((R).dbg, (buf), (p))
+#else
+#define DBG_LD(R, buf, p) (p)
+#define DBG_ST(R, buf, p) true
+#endif
+enum { DB_SRC = 0, DB_UN = 1, DB_DST = 2, DB_VDX = 3, DB_VDY = 4, DB_SOLID = 5 };
+
 template <typename T> struct GridRegs {
     const T *src, *un;
     T *dst;
@@ -627,6 +652,9 @@ template <typename T> struct GridRegs {
     const uint8_t *solid;       // solid mask of this grid, or null
     int ni, nj, pitch, plane, vpitch;
     int bcW, bcE, bcS, bcN;
+#ifdef ROEAM_DEBUG
+    DbgBufs dbg;
+#endif
 };
 
 // Cell loads of the reconstructing kernels carry the L1 priority evict_last: their window is
@@ -657,13 +685,13 @@ __device__ __forceinline__ void issue_cell(const GridRegs<T> &R, int isrc, int k
     q.solid = 0;
     if (kx != 2 && q.ky != 2) {
         const int x = q.jsrc * R.pitch + isrc;
-        q.raw[0] = ld_row<KEEP>(R.src + x);
-        q.raw[1] = ld_row<KEEP>(R.src + x + R.plane);
-        q.raw[2] = ld_row<KEEP>(R.src + x + 2 * R.plane);
-        q.raw[3] = ld_row<KEEP>(R.src + x + 3 * R.plane);
+        q.raw[0] = ld_row<KEEP>(DBG_LD(R, DB_SRC, R.src + x));
+        q.raw[1] = ld_row<KEEP>(DBG_LD(R, DB_SRC, R.src + x + R.plane));
+        q.raw[2] = ld_row<KEEP>(DBG_LD(R, DB_SRC, R.src + x + 2 * R.plane));
+        q.raw[3] = ld_row<KEEP>(DBG_LD(R, DB_SRC, R.src + x + 3 * R.plane));
         // (jsrc is a grid row, or an EXCHANGE ghost row, whose mask rows the grid also keeps)
         if constexpr (WALLS)
-            if (R.solid) q.solid = __ldg(R.solid + q.jsrc * R.ni + isrc);
+            if (R.solid) q.solid = __ldg(DBG_LD(R, DB_SOLID, R.solid + q.jsrc * R.ni + isrc));
     }
 }
 
@@ -685,7 +713,7 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
         c.q1 = q.raw[1]; c.q2 = q.raw[2]; c.q3 = q.raw[3];
         c.p = K.gm1 * vfnma(T(0.5) * q.raw[0], vfma(c.u, c.u, c.v * c.v), q.raw[3]);
         if constexpr (WALLS) {
-            if constexpr (LATE_SOLID) { if (R.solid && R.solid[q.jsrc * R.ni + isrc]) c.fl = 1; }
+            if constexpr (LATE_SOLID) { if (R.solid && *DBG_LD(R, DB_SOLID, R.solid + q.jsrc * R.ni + isrc)) c.fl = 1; }
             else if (q.solid) c.fl = 1;
         }
     }
@@ -694,7 +722,8 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
             T nx = T(0), ny = T(1);
             if constexpr (CURV) {
                 const int b = (j < 0 ? 0 : R.nj) * R.vpitch + isrc;
-                const T sx = -(R.vdy[b + 1] - R.vdy[b]), sy = K.dx + (R.vdx[b + 1] - R.vdx[b]);
+                const T sx = -(*DBG_LD(R, DB_VDY, R.vdy + b + 1) - *DBG_LD(R, DB_VDY, R.vdy + b)),
+                        sy = K.dx + (*DBG_LD(R, DB_VDX, R.vdx + b + 1) - *DBG_LD(R, DB_VDX, R.vdx + b));
                 const T l = rsq(vfma(sx, sx, sy * sy));
                 nx = sx * l; ny = sy * l;
             }
@@ -706,7 +735,8 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
                 // (the W/E boundary face of row j, ghost rows of EXCHANGE sides included)
                 const int b = clampi(j, R.bcS == BC_EXCHANGE ? -2 : 0, R.bcN == BC_EXCHANGE ? R.nj + 1 : R.nj - 1) *
                                   R.vpitch + (i < 0 ? 0 : R.ni);
-                const T sx = K.dy + (R.vdy[b + R.vpitch] - R.vdy[b]), sy = -(R.vdx[b + R.vpitch] - R.vdx[b]);
+                const T sx = K.dy + (*DBG_LD(R, DB_VDY, R.vdy + b + R.vpitch) - *DBG_LD(R, DB_VDY, R.vdy + b)),
+                        sy = -(*DBG_LD(R, DB_VDX, R.vdx + b + R.vpitch) - *DBG_LD(R, DB_VDX, R.vdx + b));
                 const T l = rsq(vfma(sx, sx, sy * sy));
                 nx = sx * l; ny = sy * l;
             }
@@ -797,6 +827,15 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         R.bcW = G.bc[0]; R.bcE = G.bc[1]; R.bcS = G.bc[2]; R.bcN = G.bc[3];
         if constexpr (CURV) { R.vdx = a.vdx + G.voff; R.vdy = a.vdy + G.voff; R.vpitch = G.vpitch; }
         else { R.vdx = R.vdy = nullptr; R.vpitch = 0; }
+#ifdef ROEAM_DEBUG
+        R.dbg.lo[DB_SRC] = (const unsigned char *)a.src; R.dbg.bytes[DB_SRC] = sizeof(T) * a.n_state;
+        R.dbg.lo[DB_UN] = (const unsigned char *)a.un; R.dbg.bytes[DB_UN] = sizeof(T) * a.n_state;
+        R.dbg.lo[DB_DST] = (const unsigned char *)a.dst; R.dbg.bytes[DB_DST] = sizeof(T) * a.n_dst;
+        R.dbg.lo[DB_VDX] = (const unsigned char *)a.vdx; R.dbg.bytes[DB_VDX] = sizeof(T) * a.n_vert;
+        R.dbg.lo[DB_VDY] = (const unsigned char *)a.vdy; R.dbg.bytes[DB_VDY] = sizeof(T) * a.n_vert;
+        R.dbg.lo[DB_SOLID] = a.solid; R.dbg.bytes[DB_SOLID] = a.n_solid;
+        R.dbg.status = a.status;
+#endif
         R.solid = (WALLS && G.soff >= 0) ? a.solid + G.soff : nullptr;
         const int ni = R.ni, nj = R.nj;
         const bool use_s1 = G.use_s1 != 0;
@@ -825,7 +864,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         auto vload = [&](int J, T &x, T &y) {
             if constexpr (CURV) {
                 const int b = clampi(J, vjlo, vjhi) * R.vpitch + clampi(i, 0, ni);
-                x = __ldg(R.vdx + b); y = __ldg(R.vdy + b);
+                x = __ldg(DBG_LD(R, DB_VDX, R.vdx + b)); y = __ldg(DBG_LD(R, DB_VDY, R.vdy + b));
             } else { x = y = T(0); }
         };
         auto px_of = [&](const WC<T> &c) {   // Eq. 97 on this lane's west face; 1 at solid sides
@@ -876,7 +915,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             T Un_next[4] = {T(0), T(0), T(0), T(0)};
             if (combine && out_lane && j < j1) {
                 const int x = j * R.pitch + i;
-                for (int k = 0; k < 4; ++k) Un_next[k] = R.un[x + k * R.plane];
+                for (int k = 0; k < 4; ++k) Un_next[k] = *DBG_LD(R, DB_UN, R.un + x + k * R.plane);
             }
             // U^(k) of row j-1 for this iteration's epilogue, issued before the faces (the
             // reconstructing curvilinear kernel, which is latency-bound: +2.4 %; the others
@@ -885,7 +924,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             if constexpr (MUSCL && CURV) {
                 if (stage_mode && out_lane && j > j0) {
                     const int x = (j - 1) * R.pitch + i;
-                    for (int k = 0; k < 4; ++k) Uk[k] = __ldg(R.src + x + k * R.plane);
+                    for (int k = 0; k < 4; ++k) Uk[k] = __ldg(DBG_LD(R, DB_SRC, R.src + x + k * R.plane));
                 }
             }
 
@@ -1031,11 +1070,12 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                             // spill), loaded above (reconstructing curvilinear), or loaded again
                             // (mostly an L1 hit)
                             const T uk = (!MUSCL && !WALLS && sizeof(T) == 4) ? Uw[k]
-                                                            : ((MUSCL && CURV) ? Uk[k] : __ldg(R.src + x + k * R.plane));
+                                                            : ((MUSCL && CURV) ? Uk[k] : __ldg(DBG_LD(R, DB_SRC, R.src + x + k * R.plane)));
                             const T upd = vfma(dt, Rs[k], uk);
                             out[k] = combine ? vfma(a.alpha, Un[k], a.beta * upd) : upd;
                         }
-                        for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = out[k];
+                        for (int k = 0; k < 4; ++k)
+                            if (DBG_ST(R, DB_DST, R.dst + x + k * R.plane)) R.dst[x + k * R.plane] = out[k];
                         if (!solid && a.want_rate) {
                             const CellPrims<T> cp = cell_prims(out[0], out[1], out[2], out[3], K);
                             if (!(out[0] > T(0)) || !(cp.p > T(0))) {
@@ -1058,7 +1098,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                             }
                         }
                     } else if (a.mode == MODE_RESIDUAL) {
-                        for (int k = 0; k < 4; ++k) R.dst[x + k * R.plane] = Rs[k];
+                        for (int k = 0; k < 4; ++k)
+                            if (DBG_ST(R, DB_DST, R.dst + x + k * R.plane)) R.dst[x + k * R.plane] = Rs[k];
                     } else if (!solid) {
                         for (int k = 0; k < 4; ++k) {
                             const double rk = (double)Rs[k];

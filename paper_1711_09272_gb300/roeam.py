@@ -15,10 +15,12 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libroeam.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "_build_debug", "libroeam.so")   # bounds-checked build (build(debug=True))
 
 ROEAM_OK, ROEAM_E_ARG, ROEAM_E_CUDA, ROEAM_E_OOM, ROEAM_E_NONPOSITIVE, ROEAM_E_NONFINITE, ROEAM_E_TIMEOUT, \
-    ROEAM_E_STATE = range(8)
-STATUS_NAMES = ["OK", "E_ARG", "E_CUDA", "E_OOM", "E_NONPOSITIVE", "E_NONFINITE", "E_TIMEOUT", "E_STATE"]
+    ROEAM_E_STATE, ROEAM_E_BOUNDS = range(9)
+STATUS_NAMES = ["OK", "E_ARG", "E_CUDA", "E_OOM", "E_NONPOSITIVE", "E_NONFINITE", "E_TIMEOUT", "E_STATE",
+                "E_BOUNDS"]
 ROEAM_NORM_L2, ROEAM_NORM_LINF = 0, 1
 
 # Entry points declared in include/roeam.h (checked by the tests).
@@ -37,7 +39,7 @@ EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_
 class RoeamError(RuntimeError):
     def __init__(self, status: int, msg: str):
         self.status = status
-        super().__init__(f"roeam {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"roeam {STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
 
 
 class roeam_params(C.Structure):
