@@ -324,9 +324,11 @@ StageArgs<T> base_args(roeam_grid *g)
     a.solid = g->solid;
     a.status = g->status;
     a.work = g->eff_dyn ? g->work : nullptr;
+#ifdef ROEAM_DEBUG
     a.n_state = a.n_dst = g->total_elems;
     a.n_vert = g->total_vert;
     a.n_solid = g->total_solid;
+#endif
     return a;
 }
 
@@ -1526,7 +1528,9 @@ roeam_status do_residual_noalloc(roeam_grid *g, int idx, double *out)
     a.un = (const T *)g->U;
     a.dst = region_t;
     a.dst_shift = G.off;
+#ifdef ROEAM_DEBUG
     a.n_dst = 4 * G.plane;
+#endif
     a.units = g->d_units_grid;
     a.tile_lo = g->h_tile_base[idx];
     a.tile_hi = g->h_tile_base[idx + 1];

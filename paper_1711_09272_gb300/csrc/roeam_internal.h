@@ -75,9 +75,11 @@ struct StageArgs {
     // each warp's first, work[1] the warps that have finished; the last warp to finish resets
     // both, so that the next launch on the handle's stream starts from zero.
     unsigned *work;
+#ifdef ROEAM_DEBUG
     // buffer sizes (elements of each state buffer and of dst, of each vertex plane buffer; bytes of
     // the solid masks), read by the bounds checks of debug builds
     long long n_state, n_dst, n_vert, n_solid;
+#endif
 };
 
 // Work-unit shapes of the stage kernel: a warp sweeps a strip tx = 32 lanes wide (2H of

@@ -722,8 +722,8 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
             T nx = T(0), ny = T(1);
             if constexpr (CURV) {
                 const int b = (j < 0 ? 0 : R.nj) * R.vpitch + isrc;
-                const T sx = -(*DBG_LD(R, DB_VDY, R.vdy + b + 1) - *DBG_LD(R, DB_VDY, R.vdy + b)),
-                        sy = K.dx + (*DBG_LD(R, DB_VDX, R.vdx + b + 1) - *DBG_LD(R, DB_VDX, R.vdx + b));
+                const T sx = -(*DBG_LD(R, DB_VDY, R.vdy + (b + 1)) - *DBG_LD(R, DB_VDY, R.vdy + b)),
+                        sy = K.dx + (*DBG_LD(R, DB_VDX, R.vdx + (b + 1)) - *DBG_LD(R, DB_VDX, R.vdx + b));
                 const T l = rsq(vfma(sx, sx, sy * sy));
                 nx = sx * l; ny = sy * l;
             }
@@ -735,8 +735,8 @@ __device__ __forceinline__ void finish_cell(const GridRegs<T> &R, const GridCoef
                 // (the W/E boundary face of row j, ghost rows of EXCHANGE sides included)
                 const int b = clampi(j, R.bcS == BC_EXCHANGE ? -2 : 0, R.bcN == BC_EXCHANGE ? R.nj + 1 : R.nj - 1) *
                                   R.vpitch + (i < 0 ? 0 : R.ni);
-                const T sx = K.dy + (*DBG_LD(R, DB_VDY, R.vdy + b + R.vpitch) - *DBG_LD(R, DB_VDY, R.vdy + b)),
-                        sy = -(*DBG_LD(R, DB_VDX, R.vdx + b + R.vpitch) - *DBG_LD(R, DB_VDX, R.vdx + b));
+                const T sx = K.dy + (*DBG_LD(R, DB_VDY, R.vdy + (b + R.vpitch)) - *DBG_LD(R, DB_VDY, R.vdy + b)),
+                        sy = -(*DBG_LD(R, DB_VDX, R.vdx + (b + R.vpitch)) - *DBG_LD(R, DB_VDX, R.vdx + b));
                 const T l = rsq(vfma(sx, sx, sy * sy));
                 nx = sx * l; ny = sy * l;
             }
@@ -915,7 +915,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             T Un_next[4] = {T(0), T(0), T(0), T(0)};
             if (combine && out_lane && j < j1) {
                 const int x = j * R.pitch + i;
-                for (int k = 0; k < 4; ++k) Un_next[k] = *DBG_LD(R, DB_UN, R.un + x + k * R.plane);
+                for (int k = 0; k < 4; ++k) Un_next[k] = *DBG_LD(R, DB_UN, R.un + (x + k * R.plane));
             }
             // U^(k) of row j-1 for this iteration's epilogue, issued before the faces (the
             // reconstructing curvilinear kernel, which is latency-bound: +2.4 %; the others
@@ -1075,7 +1075,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                             out[k] = combine ? vfma(a.alpha, Un[k], a.beta * upd) : upd;
                         }
                         for (int k = 0; k < 4; ++k)
-                            if (DBG_ST(R, DB_DST, R.dst + x + k * R.plane)) R.dst[x + k * R.plane] = out[k];
+                            if (DBG_ST(R, DB_DST, R.dst + (x + k * R.plane))) R.dst[x + k * R.plane] = out[k];
                         if (!solid && a.want_rate) {
                             const CellPrims<T> cp = cell_prims(out[0], out[1], out[2], out[3], K);
                             if (!(out[0] > T(0)) || !(cp.p > T(0))) {
@@ -1099,7 +1099,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                         }
                     } else if (a.mode == MODE_RESIDUAL) {
                         for (int k = 0; k < 4; ++k)
-                            if (DBG_ST(R, DB_DST, R.dst + x + k * R.plane)) R.dst[x + k * R.plane] = Rs[k];
+                            if (DBG_ST(R, DB_DST, R.dst + (x + k * R.plane))) R.dst[x + k * R.plane] = Rs[k];
                     } else if (!solid) {
                         for (int k = 0; k < 4; ++k) {
                             const double rk = (double)Rs[k];

@@ -1,0 +1,31 @@
+"""Register budget of the FP32 stage kernels (nvcc cross-compiles here; no GPU needed): none of
+them spills to local memory. Their occupancy is set by registers (one-warp CTAs: 128 registers
+give 16 warps per SM, 168 give 12), and a spill in the loop body costs more than it saves (a
+56-byte spill that crept in through a rewritten address expression cost the benchmark batch's
+kernel its budget), so a change that makes one spill fails here before it reaches a GPU."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_fp32_stage_kernels_do_not_spill():
+    from paper_1711_09272_gb300 import build as B
+    cmd = [B.nvcc(), *B.ARCH, *B.FLAGS, "-fmad=false", "-Xptxas", "-v", "-c",
+           os.path.join(B.CSRC, "roeam_k32.cu"), "-o", os.devnull]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    kernel, seen = None, 0
+    for line in r.stderr.splitlines():
+        m = re.search(r"Compiling entry function '(\S+)'", line)
+        if m:
+            kernel = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m and kernel and "stage_kernelIf" in kernel:
+            seen += 1
+            assert m.group(1) == "0" and m.group(2) == "0", (kernel, line)
+    assert seen >= 8, r.stderr[-2000:]
