@@ -46,6 +46,10 @@ WORKLOAD = ("batched FP32: 512 independent periodic 2D Euler grids, sizes U{32..
             "SSP-RK3 at CFL 0.5 with per-grid dt, one persistent launch per stage, CUDA-graph replay")
 
 
+def MEASURED_HBM():
+    return peaks()[0]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -126,18 +130,38 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(ncells: int):
-    """DRAM bytes per stage-kernel launch from the committed ncu summary, scaled to this launch
-    size, or None when the summary belongs to another kernel version."""
+def traffic_record():
+    """The committed ncu record of the stage kernel (profiles/stage_kernel_traffic.json), or None
+    when it belongs to another kernel version."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("kernel_hash") != kernel_hash():
+    return d if d.get("kernel_hash") == kernel_hash() else None
+
+
+def measured_traffic(ncells: int):
+    """DRAM bytes per stage-kernel launch from the committed ncu record, scaled to this launch
+    size, or None when the record belongs to another kernel version."""
+    d = traffic_record()
+    return None if d is None else d["dram_bytes_per_cell_per_launch"] * ncells
+
+
+def issue_ceiling(sm_mhz):
+    """Instruction-issue ceiling of the stage kernel from the committed ncu record: warp
+    instructions per cell and stage (w) at the sampled SM clock, 4 issue slots per SM and cycle
+    on 152 SMs: cells/s = 152 * 4 * f / w at 100 % issue, and at the issue rate ncu measured."""
+    d = traffic_record()
+    if d is None or not d.get("warp_inst_per_cell") or not sm_mhz:
         return None
-    return d["dram_bytes_per_cell_per_launch"] * ncells
+    w = d["warp_inst_per_cell"]
+    full = 152 * 4 * sm_mhz * 1e6 / w / 1e9
+    act = d.get("issue_active_pct")
+    return {"warp_inst_per_cell": w, "issue_active_pct": act, "gcell_at_full_issue": full,
+            "gcell_at_measured_issue": None if act is None else full * act / 100.0,
+            "hbm_frac_at_full_issue": full * BYTES_PER_CELL_STAGE[32] / MEASURED_HBM()}
 
 
 def dist_info():
@@ -445,7 +469,10 @@ def run_ours(args):
     b.set_state(packed, -1)
 
     tuned = None
-    if not args.no_autotune:
+    if args.tile_config is not None:
+        b.set_tile_config(args.tile_config)
+        tuned = {"chosen": args.tile_config, "fixed": True}
+    elif not args.no_autotune:
         best, ms = b.autotune(0.5, 3)   # picks the work-unit shape; restores the state
         tuned = {"chosen": int(best), "ms_per_step": [round(float(x), 4) for x in ms]}
     # warm-up (also captures the graph of this (cfl, dt) pair)
@@ -562,9 +589,9 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "stage_kernel<float> (fused flux + residual + RK stage)",
                          "bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec], "launch_ms": launch_ms,
-                         "limiter": "instruction issue, not HBM: ncu shows DRAM traffic equal to the algorithmic "
-                                    "bytes at ~25 % of DRAM peak while issue is 65 % active with 16 warps per SM "
-                                    "(124 registers); see the ncu summary of this kernel"},
+                         "limiter": "instruction issue, not HBM: DRAM traffic equals the algorithmic bytes while "
+                                    "issue is the binding resource (issue_ceiling); see the ncu summary of this "
+                                    "kernel"},
             "cpu_baseline": None if cpu_v is None else {
                 "value": cpu_all[0], "unit": UNIT, "cores": cpu_all[1], "kind": "oracle",
                 "sample": f"FP64 C oracle as independent processes, one per core, each stepping its share of "
@@ -575,6 +602,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
+        line["roofline"]["issue_ceiling"] = issue_ceiling(line["clocks"].get("sm_mhz") or 2070.0)
         if world == 1 and not args.no_extra:
             line["precision_comparison"] = precision_comparison(P, torch)
             line["curvilinear"] = warped_step_speed(P, torch)
@@ -668,6 +696,7 @@ def main():
     ap.add_argument("--grids", type=int, default=512, help="grids in the batch (512 is the benchmark workload)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work-unit shape")
+    ap.add_argument("--tile-config", type=int, default=None, help="use this work-unit shape (profiling runs)")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP32/FP64 and curvilinear side measurements")
     ap.add_argument("--only", choices=["three_d", "ablation_roe", "curvilinear", "small_configs",
                                        "precision_comparison"],
