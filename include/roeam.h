@@ -240,6 +240,15 @@ roeam_status roeam_set_halo_vertices(roeam_grid *g, int grid_idx, int side, cons
 roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const double *cons_in,
                              double *cons_out, double *dt_last);
 
+/* Single-precision host arrays: the same calls as roeam_set_state, roeam_get_state and
+ * roeam_step_host with float [4][nj][ni] host arrays (the paper has no counterpart). For an
+ * FP32 handle nothing is lost, the state being FP32, and half the bytes of the float64 calls
+ * cross the host link; an FP64 handle widens the input and rounds the output. */
+roeam_status roeam_set_state_f32(roeam_grid *g, int grid_idx, const float *cons);
+roeam_status roeam_get_state_f32(roeam_grid *g, int grid_idx, float *cons_out);
+roeam_status roeam_step_host_f32(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const float *cons_in,
+                                 float *cons_out, double *dt_last);
+
 /* FP64 norm of the residual R(U) of grid `grid_idx` over its fluid cells, per variable:
  * kind ROEAM_NORM_L2 gives sqrt(mean R^2), ROEAM_NORM_LINF gives max |R|. Synchronises. */
 roeam_status roeam_residual_norm(roeam_grid *g, int grid_idx, int kind, double out[4]);

@@ -14,4 +14,4 @@ from .roeam import (Batch, RoeamError, load_library, make_desc, roeam_cell_count
                     roeam_rk_stage, roeam_max_rate, roeam_edge_rows, roeam_set_halo, roeam_math_check,
                     roeam_step_host, roeam_set_state_device, roeam_get_state_device, roeam_rk_stage_part,
                     roeam_set_halo_solid, roeam_set_halo_vertices, ROEAM_PART_ALL, ROEAM_PART_INTERIOR,
-                    ROEAM_PART_EDGES)
+                    ROEAM_PART_EDGES, roeam_step_host_f32, roeam_set_state_f32, roeam_get_state_f32)

@@ -68,6 +68,12 @@ struct roeam_grid {
     // events (the start, then two per chunk: copied in, computed)
     cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> pipe_ev;
+    // roeam_step_host's own unit table: each chunk's units, cut so that the chunk alone gives
+    // every resident warp a unit (rebuilt when the chunks or the tile shape change)
+    int4 *d_units_pipe = nullptr;
+    int pipe_units_cap = 0, pipe_cfg = -1;
+    std::vector<std::pair<int, int>> pipe_chunks;
+    std::vector<int> pipe_tile_base;
     int precision = 32, muscl = 0, curv = 0, kind = KIND_PLAIN, count = 0;   // kind: StageKind
     size_t esize = 4;
     int tile_cfg = 0;
@@ -234,6 +240,52 @@ roeam_status setup_tiles(roeam_grid *g, int cfg)
     g->eff_dyn = tc.dyn && stage_dynamic(g->muscl, g->curv);
     for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
     g->graphs.clear();
+    return ROEAM_OK;
+}
+
+// roeam_step_host's unit table: the units of every chunk of grids, cut with the current tile
+// shape's segment height halved (down to 4 rows) until the chunk alone has a unit for every
+// resident warp, ordered by decreasing height within the chunk.
+roeam_status setup_pipe_units(roeam_grid *g, const std::vector<std::pair<int, int>> &chunks)
+{
+    const int H = g->muscl ? 2 : 1;
+    const int width = 32 - 2 * H;
+    const long long warps = g->nblocks;
+    std::vector<int4> up;
+    std::vector<int> base;
+    for (const auto &ch : chunks) {
+        base.push_back((int)up.size());
+        int ty = TILE_CFGS[g->tile_cfg].ty;
+        for (;;) {
+            long long units = 0;
+            for (int k = ch.first; k < ch.second; ++k)
+                units += (long long)((g->hg[k].ni + width - 1) / width) * ((g->hg[k].nj + ty - 1) / ty);
+            if (units >= warps || ty <= 4) break;
+            ty = std::max(4, ty / 2);
+        }
+        const size_t b0 = up.size();
+        for (int k = ch.first; k < ch.second; ++k) {
+            const GridDev &G = g->hg[k];
+            const int nty = (G.nj + ty - 1) / ty, ntx = (G.ni + width - 1) / width;
+            for (int sg = 0; sg < nty; ++sg) {
+                const int j0 = (int)((long long)sg * G.nj / nty), j1 = (int)((long long)(sg + 1) * G.nj / nty);
+                for (int st = 0; st < ntx; ++st) up.push_back(make_int4(k, st * width - H, j0, j1));
+            }
+        }
+        std::stable_sort(up.begin() + b0, up.end(), [](const int4 &a, const int4 &b) { return (a.w - a.z) > (b.w - b.z); });
+    }
+    base.push_back((int)up.size());
+    if ((int)up.size() > g->pipe_units_cap) {
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        cudaFree(g->d_units_pipe);
+        g->d_units_pipe = nullptr;
+        CUDA_TRY(cudaMalloc(&g->d_units_pipe, sizeof(int4) * up.size()));
+        g->pipe_units_cap = (int)up.size();
+    }
+    CUDA_TRY(cudaMemcpy(g->d_units_pipe, up.data(), sizeof(int4) * up.size(), cudaMemcpyHostToDevice));
+    g->pipe_chunks = chunks;
+    g->pipe_tile_base = base;
+    g->pipe_cfg = g->tile_cfg;
     return ROEAM_OK;
 }
 
@@ -448,15 +500,17 @@ roeam_status check_idx(const roeam_grid *g, int idx)
     return ROEAM_OK;
 }
 
-template <typename T>
-roeam_status do_set_state(roeam_grid *g, int idx, const double *cons)
+// (H: the host arrays' element type, double or float; the staging buffer holds either)
+template <typename T, typename H = double>
+roeam_status do_set_state(roeam_grid *g, int idx, const H *cons)
 {
     const int lo = idx < 0 ? 0 : idx, hi = idx < 0 ? g->count : idx + 1;
     const long long p0 = g->hg[lo].poff;
     const long long p1 = hi < g->count ? g->hg[hi].poff : g->total_packed;
-    CUDA_TRY(cudaMemcpyAsync(g->staging + p0, cons, sizeof(double) * (p1 - p0), cudaMemcpyHostToDevice, g->stream));
+    H *staging = (H *)g->staging;
+    CUDA_TRY(cudaMemcpyAsync(staging + p0, cons, sizeof(H) * (p1 - p0), cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaEventRecord(g->ev, g->stream));
-    CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, g->staging, (T *)g->U, g->stream));
+    CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, (const H *)staging, (T *)g->U, g->stream));
     g->launches += 1;
     roeam_status st = refresh_rate<T>(g, lo, hi);
     if (st != ROEAM_OK) return st;
@@ -465,15 +519,16 @@ roeam_status do_set_state(roeam_grid *g, int idx, const double *cons)
     return ROEAM_OK;
 }
 
-template <typename T>
-roeam_status do_get(roeam_grid *g, int idx, const void *src, double *out)
+template <typename T, typename H = double>
+roeam_status do_get(roeam_grid *g, int idx, const void *src, H *out)
 {
     const int lo = idx < 0 ? 0 : idx, hi = idx < 0 ? g->count : idx + 1;
     const long long p0 = g->hg[lo].poff;
     const long long p1 = hi < g->count ? g->hg[hi].poff : g->total_packed;
-    CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)src, g->staging, g->stream));
+    H *staging = (H *)g->staging;
+    CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)src, staging, g->stream));
     g->launches += 1;
-    CUDA_TRY(cudaMemcpyAsync(out, g->staging + p0, sizeof(double) * (p1 - p0), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(out, staging + p0, sizeof(H) * (p1 - p0), cudaMemcpyDeviceToHost, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     return ROEAM_OK;
 }
@@ -700,26 +755,27 @@ namespace {
 // copy-out stream once the computation is done. Chunks touch disjoint ranges of the staging
 // buffer, the state planes, the rate slots and the host arrays, so the three streams never
 // wait for one another except through the chunk's own two events.
-template <typename T>
-roeam_status pipe_chunk(roeam_grid *g, int lo, int hi, int nsteps, double cfl, double dt_fixed, const double *in,
-                        double *out, cudaEvent_t copied, cudaEvent_t computed)
+template <typename T, typename H>
+roeam_status pipe_chunk(roeam_grid *g, int chunk, int lo, int hi, int nsteps, double cfl, double dt_fixed,
+                        const H *in, H *out, cudaEvent_t copied, cudaEvent_t computed)
 {
     cudaStream_t s_in = g->pipe[0], s = g->pipe[1], s_out = g->pipe[2];
     const long long p0 = g->hg[lo].poff;
     const long long p1 = hi < g->count ? g->hg[hi].poff : g->total_packed;
-    CUDA_TRY(cudaMemcpyAsync(g->staging + p0, in + p0, sizeof(double) * (p1 - p0), cudaMemcpyHostToDevice, s_in));
+    H *staging = (H *)g->staging;
+    CUDA_TRY(cudaMemcpyAsync(staging + p0, in + p0, sizeof(H) * (p1 - p0), cudaMemcpyHostToDevice, s_in));
     CUDA_TRY(cudaEventRecord(copied, s_in));
     CUDA_TRY(cudaStreamWaitEvent(s, copied, 0));
-    CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, g->staging, (T *)g->U, s));
+    CUDA_TRY(Launchers<T>::pack(g->d_grids, lo, hi, g->max_cells, (const H *)staging, (T *)g->U, s));
     unsigned long long *slot0 = g->rate + (size_t)(g->step & 1) * g->count;
     CUDA_TRY(cudaMemsetAsync(slot0 + lo, 0, sizeof(unsigned long long) * (hi - lo), s));
     CUDA_TRY(Launchers<T>::rate(g->d_grids, (const GridCoef<T> *)g->d_coef, lo, hi, (const T *)g->U,
                                 (const T *)g->vdx, (const T *)g->vdy, g->solid, slot0, g->curv, s));
     T *U = (T *)g->U, *A = (T *)g->A, *B = (T *)g->B;
     StageArgs<T> a = base_args<T>(g);
-    a.units = g->d_units_grid;
-    a.tile_lo = g->h_tile_base[lo];
-    a.tile_hi = g->h_tile_base[hi];
+    a.units = g->d_units_pipe;
+    a.tile_lo = g->pipe_tile_base[chunk];
+    a.tile_hi = g->pipe_tile_base[chunk + 1];
     a.mode = MODE_STAGE;
     a.cfl = cfl;
     a.dt_fixed = dt_fixed;
@@ -738,10 +794,10 @@ roeam_status pipe_chunk(roeam_grid *g, int lo, int hi, int nsteps, double cfl, d
         a.src = B; a.dst = U; a.alpha = T(1.0 / 3.0); a.beta = T(2.0 / 3.0); a.rate_wr = wr; a.want_rate = 1;
         CUDA_TRY(Launchers<T>::stage(a, g->muscl, g->curv, g->kind, g->nblocks, s));
     }
-    CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)g->U, g->staging, s));
+    CUDA_TRY(Launchers<T>::unpack(g->d_grids, lo, hi, g->max_cells, (const T *)g->U, staging, s));
     CUDA_TRY(cudaEventRecord(computed, s));
     CUDA_TRY(cudaStreamWaitEvent(s_out, computed, 0));
-    CUDA_TRY(cudaMemcpyAsync(out + p0, g->staging + p0, sizeof(double) * (p1 - p0), cudaMemcpyDeviceToHost, s_out));
+    CUDA_TRY(cudaMemcpyAsync(out + p0, staging + p0, sizeof(H) * (p1 - p0), cudaMemcpyDeviceToHost, s_out));
     g->launches += 3 + 3ull * nsteps;
     return ROEAM_OK;
 }
@@ -926,6 +982,7 @@ void roeam_destroy_grid(roeam_grid *g)
     cudaFree(g->d_units_grid);
     cudaFree(g->d_units_all);
     cudaFree(g->d_units_part);
+    cudaFree(g->d_units_pipe);
     cudaFree(g->U);
     cudaFree(g->A);
     cudaFree(g->B);
@@ -1393,8 +1450,11 @@ roeam_status roeam_math_check(int device, int n, const double *x, double *out)
     return ROEAM_OK;
 }
 
-roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const double *cons_in,
-                             double *cons_out, double *dt_last)
+}  // extern "C"
+
+template <typename H>
+static roeam_status step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const H *cons_in, H *cons_out,
+                              double *dt_last)
 {
     if (!g || !cons_in || !cons_out) return fail(ROEAM_E_ARG, "null argument");
     if (nsteps < 1) return fail(ROEAM_E_ARG, "nsteps must be >= 1");
@@ -1413,6 +1473,10 @@ roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nst
         chunks.emplace_back(lo, hi);
         lo = hi;
     }
+    if (chunks != g->pipe_chunks || g->pipe_cfg != g->tile_cfg) {
+        roeam_status st = setup_pipe_units(g, chunks);
+        if (st != ROEAM_OK) return st;
+    }
     while (g->pipe_ev.size() < 1 + 2 * chunks.size()) {
         cudaEvent_t e;
         CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1427,8 +1491,9 @@ roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nst
         const int lo = chunks[c].first, hi = chunks[c].second;
         cudaEvent_t copied = g->pipe_ev[1 + 2 * c], computed = g->pipe_ev[2 + 2 * c];
         roeam_status st =
-            g->precision == 32 ? pipe_chunk<float>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, copied, computed)
-                               : pipe_chunk<double>(g, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, copied, computed);
+            g->precision == 32
+                ? pipe_chunk<float, H>(g, (int)c, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, copied, computed)
+                : pipe_chunk<double, H>(g, (int)c, lo, hi, nsteps, cfl, dt_fixed, cons_in, cons_out, copied, computed);
         if (st != ROEAM_OK) return st;
     }
     // the handle's stream resumes after the last copy out (which follows every computation)
@@ -1459,6 +1524,42 @@ roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nst
             }
         }
     }
+    return read_status(g);
+}
+
+extern "C" {
+
+roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const double *cons_in,
+                             double *cons_out, double *dt_last)
+{
+    return step_host<double>(g, cfl, dt_fixed, nsteps, cons_in, cons_out, dt_last);
+}
+
+roeam_status roeam_step_host_f32(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const float *cons_in,
+                                 float *cons_out, double *dt_last)
+{
+    return step_host<float>(g, cfl, dt_fixed, nsteps, cons_in, cons_out, dt_last);
+}
+
+roeam_status roeam_set_state_f32(roeam_grid *g, int grid_idx, const float *cons)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (!cons) return fail(ROEAM_E_ARG, "cons must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    return g->precision == 32 ? do_set_state<float, float>(g, grid_idx, cons)
+                              : do_set_state<double, float>(g, grid_idx, cons);
+}
+
+roeam_status roeam_get_state_f32(roeam_grid *g, int grid_idx, float *cons_out)
+{
+    roeam_status st = check_idx(g, grid_idx);
+    if (st != ROEAM_OK) return st;
+    if (!cons_out) return fail(ROEAM_E_ARG, "cons_out must be non-null");
+    CUDA_TRY(cudaSetDevice(g->device));
+    st = g->precision == 32 ? do_get<float, float>(g, grid_idx, g->U, cons_out)
+                            : do_get<double, float>(g, grid_idx, g->U, cons_out);
+    if (st != ROEAM_OK) return st;
     return read_status(g);
 }
 

@@ -132,11 +132,15 @@ struct Launchers {
                             const T *vdx, const T *vdy, const uint8_t *solid, unsigned long long *rate, int curv,
                             cudaStream_t s);
     // Packed float64 [4][nj][ni] per grid <-> pitched working-precision planes.
-    // (pack reads grid g at packed + G.poff - p_shift)
+    // (pack reads grid g at packed + G.poff - p_shift; the host-side layout in float64 or float)
     static cudaError_t pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
+                            cudaStream_t s, long long p_shift = 0);
+    static cudaError_t pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const float *packed, T *U,
                             cudaStream_t s, long long p_shift = 0);
     // (unpack reads grid g at U + G.off - u_shift and writes it at packed + G.poff - p_shift)
     static cudaError_t unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, double *packed,
+                              cudaStream_t s, long long u_shift = 0, long long p_shift = 0);
+    static cudaError_t unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, float *packed,
                               cudaStream_t s, long long u_shift = 0, long long p_shift = 0);
     // FP64 block partials of sum V*U over the fluid cells of one grid (gridDim.x * 4 doubles).
     static cudaError_t totals(const GridDev *grids, const GridCoef<T> *coef, int g, const T *U, const T *vdx,

@@ -1201,8 +1201,9 @@ __global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, const G
     if (threadIdx.x == 0 && m > T(0)) atomicMax(rate + g, rate_bits(m));
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) pack_kernel(const GridDev *grids, int g_lo, const double *packed, T *U,
+// (H: the host-side element type, double or float)
+template <typename T, typename H>
+__global__ void __launch_bounds__(256) pack_kernel(const GridDev *grids, int g_lo, const H *packed, T *U,
                                                    long long p_shift)
 {
     const GridDev &G = grids[g_lo + blockIdx.y];
@@ -1214,8 +1215,8 @@ __global__ void __launch_bounds__(256) pack_kernel(const GridDev *grids, int g_l
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g_lo, const T *U, double *packed,
+template <typename T, typename H>
+__global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g_lo, const T *U, H *packed,
                                                      long long u_shift, long long p_shift)
 {
     const GridDev &G = grids[g_lo + blockIdx.y];
@@ -1223,7 +1224,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g
     for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
         const int i = (int)(q % G.ni), j = (int)(q / G.ni);
         const long long c = G.off - u_shift + (long long)j * G.pitch + i;
-        for (int k = 0; k < 4; ++k) packed[G.poff - p_shift + k * n + q] = (double)U[c + k * G.plane];
+        for (int k = 0; k < 4; ++k) packed[G.poff - p_shift + k * n + q] = (H)U[c + k * G.plane];
     }
 }
 
@@ -1347,26 +1348,52 @@ cudaError_t Launchers<T>::rate(const GridDev *grids, const GridCoef<T> *coef, in
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t Launchers<T>::pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
+template <typename T, typename H>
+static cudaError_t launch_pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const H *packed, T *U,
                                cudaStream_t s, long long p_shift)
 {
     if (g_hi <= g_lo) return cudaSuccess;
     int bx = (max_cells + 255) / 256;
     bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
-    pack_kernel<T><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, packed, U, p_shift);
+    pack_kernel<T, H><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, packed, U, p_shift);
     return cudaGetLastError();
+}
+
+template <typename T, typename H>
+static cudaError_t launch_unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, H *packed,
+                                 cudaStream_t s, long long u_shift, long long p_shift)
+{
+    if (g_hi <= g_lo) return cudaSuccess;
+    int bx = (max_cells + 255) / 256;
+    bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
+    unpack_kernel<T, H><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, U, packed, u_shift, p_shift);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launchers<T>::pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
+                               cudaStream_t s, long long p_shift)
+{
+    return launch_pack<T, double>(grids, g_lo, g_hi, max_cells, packed, U, s, p_shift);
+}
+template <typename T>
+cudaError_t Launchers<T>::pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const float *packed, T *U,
+                               cudaStream_t s, long long p_shift)
+{
+    return launch_pack<T, float>(grids, g_lo, g_hi, max_cells, packed, U, s, p_shift);
 }
 
 template <typename T>
 cudaError_t Launchers<T>::unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, double *packed,
                                  cudaStream_t s, long long u_shift, long long p_shift)
 {
-    if (g_hi <= g_lo) return cudaSuccess;
-    int bx = (max_cells + 255) / 256;
-    bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
-    unpack_kernel<T><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, U, packed, u_shift, p_shift);
-    return cudaGetLastError();
+    return launch_unpack<T, double>(grids, g_lo, g_hi, max_cells, U, packed, s, u_shift, p_shift);
+}
+template <typename T>
+cudaError_t Launchers<T>::unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, float *packed,
+                                 cudaStream_t s, long long u_shift, long long p_shift)
+{
+    return launch_unpack<T, float>(grids, g_lo, g_hi, max_cells, U, packed, s, u_shift, p_shift);
 }
 
 template <typename T>

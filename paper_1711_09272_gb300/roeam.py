@@ -31,6 +31,7 @@ EXPORTS = ["roeam_create_grid", "roeam_destroy_grid", "roeam_set_state", "roeam_
            "roeam_tile_config_info", "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc",
            "roeam_rk_stage", "roeam_rk_stage_part", "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo",
            "roeam_set_halo_solid", "roeam_set_halo_vertices", "roeam_math_check", "roeam_step_host",
+           "roeam_set_state_f32", "roeam_get_state_f32", "roeam_step_host_f32",
            "roeam3_create_grid", "roeam3_destroy_grid", "roeam3_set_state", "roeam3_get_state",
            "roeam3_flux_residual", "roeam3_rk_step", "roeam3_conserved_totals", "roeam3_check",
            "roeam3_launch_count"]
@@ -103,6 +104,9 @@ def load_library(path: str = LIB_PATH):
     lib.roeam_set_halo_vertices.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.roeam_math_check.argtypes = [C.c_int, C.c_int, dp, dp]
     lib.roeam_step_host.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp, vp]
+    lib.roeam_step_host_f32.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp, vp]
+    lib.roeam_set_state_f32.argtypes = [vp, C.c_int, vp]
+    lib.roeam_get_state_f32.argtypes = [vp, C.c_int, vp]
     lib.roeam_max_rate.argtypes = [vp, dp]
     lib.roeam_edge_rows.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
     lib.roeam_set_halo.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
@@ -122,7 +126,8 @@ def load_library(path: str = LIB_PATH):
                  "roeam_residual_norm", "roeam_conserved_totals", "roeam_check", "roeam_tile_config_info",
                  "roeam_set_tile_config", "roeam_autotune", "roeam_flux_residual_noalloc", "roeam_rk_stage",
                  "roeam_max_rate", "roeam_edge_rows", "roeam_set_halo", "roeam_math_check", "roeam_step_host",
-                 "roeam_rk_stage_part", "roeam_set_halo_solid", "roeam_set_halo_vertices",
+                 "roeam_rk_stage_part", "roeam_set_halo_solid", "roeam_set_halo_vertices", "roeam_step_host_f32",
+                 "roeam_set_state_f32", "roeam_get_state_f32",
                  "roeam3_create_grid",
                  "roeam3_set_state", "roeam3_get_state", "roeam3_flux_residual", "roeam3_rk_step",
                  "roeam3_conserved_totals", "roeam3_check"):
@@ -247,6 +252,21 @@ def roeam_step_host(h: int, cfl: float, dt_fixed: float, nsteps: int, cons_in, c
     _check(load_library().roeam_step_host(C.c_void_p(h), cfl, dt_fixed, nsteps, C.c_void_p(_ptr(cons_in)),
                                           C.c_void_p(_ptr(cons_out)),
                                           C.c_void_p(_ptr(dt_last) if dt_last is not None else None)))
+
+
+def roeam_step_host_f32(h: int, cfl: float, dt_fixed: float, nsteps: int, cons_in, cons_out, dt_last=None) -> None:
+    """roeam_step_host with float32 host arrays (numpy float32 or torch float32, pinned or not)."""
+    _check(load_library().roeam_step_host_f32(C.c_void_p(h), cfl, dt_fixed, nsteps, C.c_void_p(_ptr(cons_in)),
+                                              C.c_void_p(_ptr(cons_out)),
+                                              C.c_void_p(_ptr(dt_last) if dt_last is not None else None)))
+
+
+def roeam_set_state_f32(h: int, grid_idx: int, cons) -> None:
+    _check(load_library().roeam_set_state_f32(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(cons))))
+
+
+def roeam_get_state_f32(h: int, grid_idx: int, out) -> None:
+    _check(load_library().roeam_get_state_f32(C.c_void_p(h), grid_idx, C.c_void_p(_ptr(out))))
 
 
 def roeam_math_check(x, device: int = 0) -> np.ndarray:

@@ -13,7 +13,7 @@ def declared_functions():
     for h in ("roeam.h", "roeam3.h"):
         text = open(os.path.join(ROOT, "include", h)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names |= set(re.findall(r"\b(roeam3?_[a-z_]+)\s*\(", text))
+        names |= set(re.findall(r"\b(roeam3?_[a-z0-9_]+)\s*\(", text))
     return sorted(names)
 
 

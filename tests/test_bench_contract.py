@@ -54,7 +54,8 @@ def test_gpu_arm_line():
     assert r["traffic"] is None or r["traffic"] > 0
     assert d["gpu_launches"] == 3 * steps
     e = d["e2e"]
-    assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 8 * 4 * cells
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 4 * 4 * cells
+    assert e["float64_host_arrays"]["h2d_bytes_per_step"] == 8 * 4 * cells
     c = d["clocks"]
     assert "sm_mhz" in c and "sm_max_mhz" in c and isinstance(c["reasons"], list)
 

@@ -87,3 +87,37 @@ def test_device_io_rejects_host_memory():
         assert e.value.status == 1
         with pytest.raises(P().RoeamError):
             b.get_state_device(host, 0)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_single_precision_host_arrays(prec):
+    """roeam_set_state_f32 / roeam_get_state_f32 / roeam_step_host_f32: float32 host arrays give
+    the state the float64 calls give for the same (float32-representable) input, bit for bit
+    after rounding the float64 output to float32; an FP32 handle loses nothing either way."""
+    import torch
+    specs, states = W.batch(count=30, seed=91, ni_range=(20, 150), nj_range=(10, 90))
+    packed32 = np.concatenate([U.ravel() for U in states]).astype(np.float32)
+    packed64 = packed32.astype(np.float64)
+    with P().Batch(specs, precision=prec) as b:
+        b.set_state(packed64, -1)
+        dt_ref = b.step(0.5, nsteps=3, want_dt=True)
+        ref = np.concatenate([u.ravel() for u in b.get_states()])
+    with P().Batch(specs, precision=prec) as b:
+        P().roeam_set_state_f32(b.handle, -1, packed32)
+        out = np.empty_like(packed32)
+        P().roeam_get_state_f32(b.handle, -1, out)
+        assert np.array_equal(out, packed32)
+        b.step(0.5, nsteps=3)
+        P().roeam_get_state_f32(b.handle, -1, out)
+        assert np.array_equal(out, ref.astype(np.float32))
+    h_in = torch.from_numpy(packed32.copy()).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    dt = np.zeros(len(specs))
+    with P().Batch(specs, precision=prec) as b:
+        P().roeam_step_host_f32(b.handle, 0.5, 0.0, 3, h_in, h_out, dt)
+        got = h_out.numpy().copy()
+        assert np.array_equal(np.concatenate([u.ravel() for u in b.get_states()]).astype(np.float32), got)
+    assert np.array_equal(got, ref.astype(np.float32))
+    assert np.array_equal(dt, dt_ref)
+    if prec == 32:   # an FP32 state read back in float64 is exact
+        assert np.array_equal(ref, ref.astype(np.float32).astype(np.float64))

@@ -286,10 +286,12 @@ def test_batch_mixing_schemes(prec):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
-def test_step_host_matches_separate_calls(prec):
-    """roeam_step_host (chunked, copies in, steps and copies out on three streams) gives exactly the state and
-    time steps of set_state + rk_step + get_state, for a batch spanning many chunks, with
-    page-locked and with pageable host arrays."""
+@pytest.mark.parametrize("cfg", [0, 4, 8])
+def test_step_host_matches_separate_calls(prec, cfg):
+    """roeam_step_host (chunked, copies in, steps and copies out on three streams; each chunk's
+    units cut from the tile shape so the chunk fills the resident warps) gives exactly the state
+    and time steps of set_state + rk_step + get_state, for a batch spanning many chunks, with
+    page-locked and with pageable host arrays, and with the tile shape changed between calls."""
     import torch
     specs, states = W.batch(40, seed=77)
     packed = np.concatenate([s.ravel() for s in states])
@@ -297,7 +299,10 @@ def test_step_host_matches_separate_calls(prec):
     h_out = torch.empty_like(h_in).pin_memory()
     dt_a = np.zeros(len(specs))
     with P().Batch(specs, precision=prec) as b:
-        P().roeam_step_host(b.handle, 0.5, 0.0, 3, h_in, h_out, dt_a)
+        b.set_tile_config(cfg)
+        P().roeam_step_host(b.handle, 0.5, 0.0, 1, h_in, h_out, dt_a)
+        b.set_tile_config((cfg + 1) % len(TILE_CFGS))
+        P().roeam_step_host(b.handle, 0.5, 0.0, 2, h_out, h_out, dt_a)
         got = h_out.numpy().copy()
         assert np.array_equal(np.concatenate([u.ravel() for u in b.get_states()]), got)
     with P().Batch(specs, precision=prec) as b:
