@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "roeam.h"
 #include "roeam_internal.h"
 
@@ -46,6 +48,12 @@ roeam_status fail(roeam_status st, const char *fmt, ...)
 long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
 
 constexpr int GRAPH_STEPS = 8;   // SSP-RK3 steps per captured graph (an even number)
+
+// NVTX range around a library call (visible in a profiler's timeline; free without one).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 // Autotuner results of this process, by workload (see tune_key).
 struct TuneResult { int best; double ms[NUM_TILE_CFGS]; };
@@ -926,9 +934,16 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
     CREATE_TRY(cudaMalloc(&g->U, sbytes));
     CREATE_TRY(cudaMalloc(&g->A, sbytes));
     CREATE_TRY(cudaMalloc(&g->B, sbytes));
-    CREATE_TRY(cudaMemset(g->U, 0, sbytes));
-    CREATE_TRY(cudaMemset(g->A, 0, sbytes));
-    CREATE_TRY(cudaMemset(g->B, 0, sbytes));
+#ifdef ROEAM_DEBUG
+    // bounds-checked builds fill the state buffers with NaN (padding columns, ghost rows not yet
+    // set): a read of them that reached a written cell would show as a non-finite state
+    const int fill = 0xFF;
+#else
+    const int fill = 0;
+#endif
+    CREATE_TRY(cudaMemset(g->U, fill, sbytes));
+    CREATE_TRY(cudaMemset(g->A, fill, sbytes));
+    CREATE_TRY(cudaMemset(g->B, fill, sbytes));
     if (g->curv) {
         CREATE_TRY(cudaMalloc(&g->vdx, g->esize * (size_t)g->total_vert));
         CREATE_TRY(cudaMalloc(&g->vdy, g->esize * (size_t)g->total_vert));
@@ -1009,6 +1024,7 @@ void roeam_destroy_grid(roeam_grid *g)
 
 roeam_status roeam_set_state(roeam_grid *g, int grid_idx, const double *cons)
 {
+    const Range range_("roeam_set_state");
     roeam_status st = check_idx(g, grid_idx);
     if (st != ROEAM_OK) return st;
     if (!cons) return fail(ROEAM_E_ARG, "cons must be non-null");
@@ -1058,6 +1074,7 @@ roeam_status roeam_get_state_device(roeam_grid *g, int grid_idx, double *cons_ou
 
 roeam_status roeam_get_state(roeam_grid *g, int grid_idx, double *cons_out)
 {
+    const Range range_("roeam_get_state");
     roeam_status st = check_idx(g, grid_idx);
     if (st != ROEAM_OK) return st;
     if (!cons_out) return fail(ROEAM_E_ARG, "cons_out must be non-null");
@@ -1069,6 +1086,7 @@ roeam_status roeam_get_state(roeam_grid *g, int grid_idx, double *cons_out)
 
 roeam_status roeam_flux_residual(roeam_grid *g, int grid_idx, double *res_out)
 {
+    const Range range_("roeam_flux_residual");
     roeam_status st = check_idx(g, grid_idx);
     if (st != ROEAM_OK) return st;
     for (int k = 0; k < g->count; ++k)
@@ -1079,6 +1097,7 @@ roeam_status roeam_flux_residual(roeam_grid *g, int grid_idx, double *res_out)
 
 roeam_status roeam_rk_step(roeam_grid *g, double cfl, double dt_fixed, int nsteps, double *dt_last)
 {
+    const Range range_("roeam_rk_step");
     if (!g) return fail(ROEAM_E_ARG, "null handle");
     if (nsteps < 0) return fail(ROEAM_E_ARG, "nsteps must be >= 0");
     if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(ROEAM_E_ARG, "need cfl > 0 or dt_fixed > 0");
@@ -1171,6 +1190,7 @@ roeam_status roeam_set_tile_config(roeam_grid *g, int cfg)
 
 roeam_status roeam_autotune(roeam_grid *g, double cfl, int steps, int *best_cfg, double *ms_per_step)
 {
+    const Range range_("roeam_autotune");
     if (!g) return fail(ROEAM_E_ARG, "null handle");
     if (steps < 1 || !(cfl > 0.0)) return fail(ROEAM_E_ARG, "need steps >= 1 and cfl > 0");
     for (int k = 0; k < g->count; ++k)
@@ -1306,6 +1326,7 @@ roeam_status roeam_rk_stage(roeam_grid *g, int stage, double dt)
 
 roeam_status roeam_rk_stage_part(roeam_grid *g, int stage, double dt, int part)
 {
+    const Range range_("roeam_rk_stage_part");
     if (!g) return fail(ROEAM_E_ARG, "null handle");
     if (stage < 0 || stage > 2) return fail(ROEAM_E_ARG, "stage must be 0, 1 or 2");
     if (part < ROEAM_PART_ALL || part > ROEAM_PART_EDGES) return fail(ROEAM_E_ARG, "part must be 0, 1 or 2");
@@ -1456,6 +1477,7 @@ template <typename H>
 static roeam_status step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const H *cons_in, H *cons_out,
                               double *dt_last)
 {
+    const Range range_("roeam_step_host");
     if (!g || !cons_in || !cons_out) return fail(ROEAM_E_ARG, "null argument");
     if (nsteps < 1) return fail(ROEAM_E_ARG, "nsteps must be >= 1");
     if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(ROEAM_E_ARG, "need cfl > 0 or dt_fixed > 0");

@@ -466,3 +466,27 @@ def test_l2_error_after_n_steps(prec):
     assert l2.max() <= (1e-13 if prec == 64 else 1e-5), l2   # (measured 2e-15 and 2.3e-6)
     warnings.warn(f"FP{prec} L2 state difference from the oracle after 100 steps: " +
                   " ".join(f"{x:.2e}" for x in l2))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_injected_nan_and_bad_steps_are_reported(prec):
+    """Host-side fault injection: a NaN in the state given to set_state is reported as
+    ROEAM_E_NONFINITE after the next step (nothing traps, the context stays usable), and a
+    non-positive fixed time step or CFL is refused before any work."""
+    import paper_1711_09272_gb300 as pkg
+    spec = W.GridSpec(ni=24, nj=20, dx=0.05, dy=0.05)
+    U = W.free_stream(spec)
+    U[1, 7, 9] = np.nan
+    with pkg.Batch([spec], precision=prec) as b:
+        b.set_state(U, 0)
+        b.step(cfl=0.5, dt_fixed=1e-3, nsteps=1)
+        with pytest.raises(pkg.RoeamError) as e:
+            b.check()
+        assert e.value.status == 5
+        b.set_state(W.free_stream(spec), 0)      # the handle keeps working
+        b.step(cfl=0.5, nsteps=2)
+        b.check()
+        for cfl, dt in ((0.0, 0.0), (-0.5, 0.0), (0.5, float("nan"))):
+            with pytest.raises(pkg.RoeamError) as e:
+                b.step(cfl=cfl, dt_fixed=dt, nsteps=1)
+            assert e.value.status == 1
