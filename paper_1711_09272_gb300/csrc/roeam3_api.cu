@@ -136,17 +136,42 @@ roeam_status upload_coef3(roeam3_grid *g, const roeam3_grid_desc *d)
 }
 
 // Work units: 30 x 6 columns of a plane (TILE3_X x TILE3_Y written cells) by a segment of
-// planes; segments shortened until there are about four units per resident CTA.
+// planes. The number of segments per column starts at about four units per resident CTA and is
+// then chosen, up to twice that, to fill the last round of units over the CTAs (all units cost
+// about the same): the 256^3 Taylor-Green vortex had 1548 units over 304 CTAs, a sixth round
+// 9 % full; 7 segments give 2709 units in 8.9 rounds. Each extra segment re-reads two planes,
+// which the choice weighs at half a plane of work each.
 roeam_status setup_units3(roeam3_grid *g, int num_sms)
 {
     const int occ = g->precision == 32 ? Launchers3<float>::stage_occupancy(g->nscal)
                                        : Launchers3<double>::stage_occupancy(g->nscal);
     g->nblocks = std::max(1, occ * num_sms);
-    long long columns = 0;
-    for (const GridDev3 &G : g->hg)
+    long long columns = 0, nk_max = 1;
+    for (const GridDev3 &G : g->hg) {
         columns += (long long)((G.ni + TILE3_X - 1) / TILE3_X) * ((G.nj + TILE3_Y - 1) / TILE3_Y);
+        nk_max = std::max<long long>(nk_max, G.nk);
+    }
     const long long target = 4ll * g->nblocks;
-    const long long nseg = std::max(1ll, (target + columns - 1) / columns);
+    const long long nseg0 = std::max(1ll, (target + columns - 1) / columns);
+    long long nseg = nseg0;
+    {
+        double best = -1.0;
+        for (long long n = nseg0; n <= 2 * nseg0; ++n) {
+            long long units = 0;
+            double planes = 0.0, extra = 0.0;
+            for (const GridDev3 &G : g->hg) {
+                const long long cols = (long long)((G.ni + TILE3_X - 1) / TILE3_X) * ((G.nj + TILE3_Y - 1) / TILE3_Y);
+                const int zs = std::max(4, (int)((G.nk + n - 1) / n));
+                const long long segs = (G.nk + zs - 1) / zs;
+                units += cols * segs;
+                planes += (double)cols * G.nk;
+                extra += (double)cols * segs;   // two re-read planes per segment, at half a plane each
+            }
+            const long long rounds = (units + g->nblocks - 1) / g->nblocks;
+            const double eff = (double)units / (double)(rounds * g->nblocks) * planes / (planes + extra);
+            if (eff > best + 1e-9) { best = eff; nseg = n; }
+        }
+    }
     std::vector<int4> units;
     for (int gi = 0; gi < g->count; ++gi) {
         const GridDev3 &G = g->hg[gi];
