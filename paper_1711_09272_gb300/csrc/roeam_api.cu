@@ -1184,6 +1184,7 @@ roeam_status roeam_set_tile_config(roeam_grid *g, int cfg)
 {
     if (!g) return fail(ROEAM_E_ARG, "null handle");
     if (cfg < 0 || cfg >= NUM_TILE_CFGS) return fail(ROEAM_E_ARG, "tile config %d out of range", cfg);
+    if (g->part_next != 0) return fail(ROEAM_E_STATE, "the edge part of a stage is due");
     CUDA_TRY(cudaSetDevice(g->device));
     return setup_tiles(g, cfg);
 }
@@ -1193,6 +1194,7 @@ roeam_status roeam_autotune(roeam_grid *g, double cfl, int steps, int *best_cfg,
     const Range range_("roeam_autotune");
     if (!g) return fail(ROEAM_E_ARG, "null handle");
     if (steps < 1 || !(cfl > 0.0)) return fail(ROEAM_E_ARG, "need steps >= 1 and cfl > 0");
+    if (g->stage_next != 0 || g->part_next != 0) return fail(ROEAM_E_STATE, "a step run by roeam_rk_stage is unfinished");
     for (int k = 0; k < g->count; ++k)
         if (!g->state_set[k]) return fail(ROEAM_E_STATE, "state of grid %d not set", k);
     CUDA_TRY(cudaSetDevice(g->device));

@@ -490,3 +490,37 @@ def test_injected_nan_and_bad_steps_are_reported(prec):
             with pytest.raises(pkg.RoeamError) as e:
                 b.step(cfl=cfl, dt_fixed=dt, nsteps=1)
             assert e.value.status == 1
+
+
+def test_autotuner_picks_a_shape_and_caches_it_per_workload():
+    """roeam_autotune times the distinct layouts, keeps the fastest and restores the state; a
+    second handle on the same workload gets the same choice and figures without timing, and a
+    different workload is timed afresh."""
+    import time
+    specs, states = W.batch(96, seed=31)
+    with P().Batch(specs, precision=32) as b:
+        b.set_states(states)
+        U0 = b.get_states()
+        t0 = time.perf_counter()
+        best, ms = b.autotune(0.5, 3)
+        t_first = time.perf_counter() - t0
+        assert 0 <= best < len(TILE_CFGS) and len(ms) == len(TILE_CFGS)
+        assert ms[best] == min(ms) and all(m > 0 for m in ms)
+        for k, u in enumerate(b.get_states()):
+            assert np.array_equal(u, U0[k])          # the state is restored
+        b.step(0.5, nsteps=2)
+        Ua = b.get_states()
+    with P().Batch(specs, precision=32) as b:
+        b.set_states(states)
+        t0 = time.perf_counter()
+        best2, ms2 = b.autotune(0.5, 3)
+        t_second = time.perf_counter() - t0
+        assert best2 == best and list(ms2) == list(ms)
+        b.step(0.5, nsteps=2)
+        assert all(np.array_equal(x, y) for x, y in zip(b.get_states(), Ua))
+    assert t_second < t_first
+    other = [W.with_params(s, recon=2) for s in specs]
+    with P().Batch(other, precision=32) as b:
+        b.set_states(states)
+        _, ms3 = b.autotune(0.5, 3)
+        assert list(ms3) != list(ms)
