@@ -130,10 +130,10 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_record():
-    """The committed ncu record of the stage kernel (profiles/stage_kernel_traffic.json), or None
-    when it belongs to another kernel version."""
-    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+def traffic_record(name="stage_kernel_traffic.json"):
+    """A committed ncu record of a stage kernel (profiles/<name>: the headline kernel's, or the
+    reconstructing curvilinear kernel's), or None when it belongs to another kernel version."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             d = json.load(f)
@@ -149,11 +149,11 @@ def measured_traffic(ncells: int):
     return None if d is None else d["dram_bytes_per_cell_per_launch"] * ncells
 
 
-def issue_ceiling(sm_mhz):
-    """Instruction-issue ceiling of the stage kernel from the committed ncu record: warp
+def issue_ceiling(sm_mhz, record="stage_kernel_traffic.json", bytes_per_cell=BYTES_PER_CELL_STAGE[32]):
+    """Instruction-issue ceiling of a stage kernel from its committed ncu record: warp
     instructions per cell and stage (w) at the sampled SM clock, 4 issue slots per SM and cycle
     on 152 SMs: cells/s = 152 * 4 * f / w at 100 % issue, and at the issue rate ncu measured."""
-    d = traffic_record()
+    d = traffic_record(record)
     if d is None or not d.get("warp_inst_per_cell") or not sm_mhz:
         return None
     w = d["warp_inst_per_cell"]
@@ -161,7 +161,7 @@ def issue_ceiling(sm_mhz):
     act = d.get("issue_active_pct")
     return {"warp_inst_per_cell": w, "issue_active_pct": act, "gcell_at_full_issue": full,
             "gcell_at_measured_issue": None if act is None else full * act / 100.0,
-            "hbm_frac_at_full_issue": full * BYTES_PER_CELL_STAGE[32] / MEASURED_HBM()}
+            "hbm_frac_at_full_issue": full * bytes_per_cell / MEASURED_HBM()}
 
 
 def dist_info():
@@ -299,9 +299,12 @@ def warped_step_speed(P, torch, steps=20):
     ms, _ = time_single(P, torch, spec, U, 32, steps)
     v = spec.ncells * 3 / (ms * 1e-3) / 1e9
     peak, kind = peaks()
+    rec = traffic_record("stage_kernel_curvilinear_record.json")
     return {"workload": "warped step 4096x4096 FP32, MUSCL van Leer, solid block, walls/inflow/outflow",
             "gcell_updates_per_s_per_stage": v, "ms_per_step": ms,
-            "hbm_frac": v * (128.0 / 3 + 8) / peak, "peak_gbs": peak, "peak_kind": kind}
+            "hbm_frac": v * (128.0 / 3 + 8) / peak, "peak_gbs": peak, "peak_kind": kind,
+            "traffic_bytes_per_cell": None if rec is None else rec["dram_bytes_per_cell_per_launch"],
+            "issue_ceiling": issue_ceiling(2070.0, "stage_kernel_curvilinear_record.json", 128.0 / 3 + 8)}
 
 
 def three_d_speed(P, torch, n=256, nscal=1, steps=20):
