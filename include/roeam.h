@@ -232,9 +232,10 @@ roeam_status roeam_set_halo_vertices(roeam_grid *g, int grid_idx, int side, cons
 /* The host-resident form of a step: loads every grid from cons_in (host float64, the layout of
  * roeam_set_state with grid_idx = -1), advances nsteps SSP-RK3 steps as roeam_rk_step does, and
  * writes the result to cons_out (same layout; it may equal cons_in), overlapping the copies
- * with the computation: the grids go through in chunks of about an eighth of the cells on three
- * internal streams (copies in, computation, copies out), so that one chunk is copied in while
- * the one before it is stepped and an earlier one is copied out.
+ * with the computation: the grids go through in ten chunks of whole grids, small at both ends
+ * (about 1:2:3:4:4:4:4:3:2:1 of the cells), on three internal streams (copies in, computation,
+ * copies out), so that one chunk is copied in while the one before it is stepped and an earlier
+ * one is copied out.
  * Page-locked host arrays make the copies asynchronous. The device state afterwards equals
  * cons_out. dt_last as in roeam_rk_step. Synchronises; reports device errors. */
 roeam_status roeam_step_host(roeam_grid *g, double cfl, double dt_fixed, int nsteps, const double *cons_in,

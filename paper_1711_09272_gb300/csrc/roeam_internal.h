@@ -121,22 +121,29 @@ __host__ __device__ constexpr bool stage_dynamic(int muscl, int curv) { return !
 // grid uses an ablation variant of the flux (every face on the scalar path).
 enum StageKind { KIND_PLAIN = 0, KIND_WALLS = 1, KIND_ABLATION = 2 };
 
+// What a pack needs to take the time-step rate of the state it writes: the grids' coefficients,
+// vertex displacements and solid masks, and the rate slots it raises with atomicMax.
+template <typename T> struct RateOut {
+    const GridCoef<T> *coef = nullptr;
+    const T *vdx = nullptr, *vdy = nullptr;
+    const uint8_t *solid = nullptr;
+    unsigned long long *rate = nullptr;
+    int curv = 0;
+};
+
 template <typename T>
 struct Launchers {
     // Fused face-flux / residual / stage kernel over tiles [tile_lo, tile_hi).
     static cudaError_t stage(const StageArgs<T> &a, int muscl, int curv, int kind, int nblocks, cudaStream_t s);
     // Largest resident CTAs per SM of a stage-kernel variant (for persistent launches).
     static int stage_occupancy(int muscl, int curv, int kind);
-    // Max signal-speed rate of a state into rate[g] (slot zeroed first by the caller).
-    static cudaError_t rate(const GridDev *grids, const GridCoef<T> *coef, int g_lo, int g_hi, const T *U,
-                            const T *vdx, const T *vdy, const uint8_t *solid, unsigned long long *rate, int curv,
-                            cudaStream_t s);
     // Packed float64 [4][nj][ni] per grid <-> pitched working-precision planes.
-    // (pack reads grid g at packed + G.poff - p_shift; the host-side layout in float64 or float)
+    // (pack reads grid g at packed + G.poff - p_shift; the host-side layout in float64 or float;
+    //  with ro it also writes the packed state's rate into ro->rate[g], zeroed by the caller)
     static cudaError_t pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
-                            cudaStream_t s, long long p_shift = 0);
+                            cudaStream_t s, long long p_shift = 0, const RateOut<T> *ro = nullptr);
     static cudaError_t pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const float *packed, T *U,
-                            cudaStream_t s, long long p_shift = 0);
+                            cudaStream_t s, long long p_shift = 0, const RateOut<T> *ro = nullptr);
     // (unpack reads grid g at U + G.off - u_shift and writes it at packed + G.poff - p_shift)
     static cudaError_t unpack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const T *U, double *packed,
                               cudaStream_t s, long long u_shift = 0, long long p_shift = 0);

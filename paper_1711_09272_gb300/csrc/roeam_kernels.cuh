@@ -1171,60 +1171,91 @@ template <int NT, typename T> __device__ __forceinline__ T block_max(T v, T *red
 }
 
 // ------------------------------------------------------------------ small kernels
-// Largest rate of every fluid cell of grids [g_lo, g_hi) (blockIdx.y = grid).
-template <typename T, bool CURV>
-__global__ void __launch_bounds__(256) rate_kernel(const GridDev *grids, const GridCoef<T> *coef, int g_lo, const T *U,
-                                                   const T *vdx, const T *vdy, const uint8_t *solid,
-                                                   unsigned long long *rate)
+// Host layout [4][nj][ni] per grid (H: float64 or float) <-> pitched planes, blockIdx.y = grid.
+// Each thread moves IO_PER cells a stride of gridDim.x * 256 apart, all of their loads issued
+// before the first store, so that a thread has IO_PER x 4 loads in flight instead of one DRAM
+// latency per cell; indices are 32-bit (a grid holds at most 2^28 cells). With RATE the pack
+// also takes the time-step rate of the state it writes, the largest cell_rate over the fluid
+// cells (the functions the stage kernel's third stage applies to the state it writes, so a state
+// loaded from the host gives the dt bit for bit that the same state gives once stepped into),
+// in the same pass.
+constexpr int IO_PER = 4;
+
+template <typename T, typename H, bool RATE, bool CURV>
+__global__ void __launch_bounds__(256) pack_kernel(const GridDev *grids, int g_lo, const H *__restrict__ packed,
+                                                   T *__restrict__ U, long long p_shift, RateOut<T> ro)
 {
     __shared__ T red[8];
     const int g = g_lo + blockIdx.y;
     const GridDev &G = grids[g];
-    const GridCoef<T> K = coef[g];
-    const long long n = (long long)G.ni * G.nj;
+    const unsigned ni = (unsigned)G.ni, n = ni * (unsigned)G.nj, stride = gridDim.x * 256u;
+    const H *__restrict__ src = packed + (G.poff - p_shift);
+    T *__restrict__ dst = U + G.off;
+    const long long pitch = G.pitch, plane = G.plane;
     T m = T(0);
-    for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
-        const int i = (int)(q % G.ni), j = (int)(q / G.ni);
-        if (G.soff >= 0 && solid[G.soff + q]) continue;
-        const long long c = G.off + (long long)j * G.pitch + i;
-        CellGeom<T> cg;
-        if (CURV) {
-            const long long b = G.voff + (long long)j * G.vpitch + i;
-            cg = cell_geom(vdx[b], vdx[b + 1], vdx[b + G.vpitch], vdx[b + G.vpitch + 1], vdy[b], vdy[b + 1],
-                           vdy[b + G.vpitch], vdy[b + G.vpitch + 1], K.dx, K.dy);
-        } else {
-            cg.Xx = K.dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = K.dx; cg.V = K.V;
+    for (unsigned q0 = blockIdx.x * 256u + threadIdx.x; q0 < n; q0 += IO_PER * stride) {
+        T v[IO_PER][4];
+#pragma unroll
+        for (int e = 0; e < IO_PER; ++e) {
+            const unsigned q = q0 + e * stride;
+            if (q < n)
+                for (int k = 0; k < 4; ++k) v[e][k] = T(src[(long long)k * n + q]);
         }
-        m = vmax(m, cell_rate<CURV>(cell_prims(U[c], U[c + G.plane], U[c + 2 * G.plane], U[c + 3 * G.plane], K), cg, K));
+#pragma unroll
+        for (int e = 0; e < IO_PER; ++e) {
+            const unsigned q = q0 + e * stride;
+            if (q >= n) break;
+            const unsigned j = q / ni, i = q - j * ni;
+            const long long c = (long long)j * pitch + i;
+            for (int k = 0; k < 4; ++k) dst[c + k * plane] = v[e][k];
+            if constexpr (RATE) {
+                if (G.soff >= 0 && ro.solid[G.soff + q]) continue;
+                const GridCoef<T> &K = ro.coef[g];
+                CellGeom<T> cg;
+                if constexpr (CURV) {
+                    const T *vx = ro.vdx + G.voff, *vy = ro.vdy + G.voff;
+                    const long long b = (long long)j * G.vpitch + i;
+                    cg = cell_geom(vx[b], vx[b + 1], vx[b + G.vpitch], vx[b + G.vpitch + 1], vy[b], vy[b + 1],
+                                   vy[b + G.vpitch], vy[b + G.vpitch + 1], K.dx, K.dy);
+                } else {
+                    cg.Xx = K.dy; cg.Xy = T(0); cg.Yx = T(0); cg.Yy = K.dx; cg.V = K.V;
+                }
+                m = vmax(m, cell_rate<CURV>(cell_prims(v[e][0], v[e][1], v[e][2], v[e][3], K), cg, K));
+            }
+        }
     }
-    m = block_max<256>(m, red);
-    if (threadIdx.x == 0 && m > T(0)) atomicMax(rate + g, rate_bits(m));
+    if constexpr (RATE) {
+        m = block_max<256>(m, red);
+        if (threadIdx.x == 0 && m > T(0)) atomicMax(ro.rate + g, rate_bits(m));
+    }
 }
 
-// (H: the host-side element type, double or float)
 template <typename T, typename H>
-__global__ void __launch_bounds__(256) pack_kernel(const GridDev *grids, int g_lo, const H *packed, T *U,
-                                                   long long p_shift)
+__global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g_lo, const T *__restrict__ U,
+                                                     H *__restrict__ packed, long long u_shift, long long p_shift)
 {
     const GridDev &G = grids[g_lo + blockIdx.y];
-    const long long n = (long long)G.ni * G.nj;
-    for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
-        const int i = (int)(q % G.ni), j = (int)(q / G.ni);
-        const long long c = G.off + (long long)j * G.pitch + i;
-        for (int k = 0; k < 4; ++k) U[c + k * G.plane] = T(packed[G.poff - p_shift + k * n + q]);
-    }
-}
-
-template <typename T, typename H>
-__global__ void __launch_bounds__(256) unpack_kernel(const GridDev *grids, int g_lo, const T *U, H *packed,
-                                                     long long u_shift, long long p_shift)
-{
-    const GridDev &G = grids[g_lo + blockIdx.y];
-    const long long n = (long long)G.ni * G.nj;
-    for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
-        const int i = (int)(q % G.ni), j = (int)(q / G.ni);
-        const long long c = G.off - u_shift + (long long)j * G.pitch + i;
-        for (int k = 0; k < 4; ++k) packed[G.poff - p_shift + k * n + q] = (H)U[c + k * G.plane];
+    const unsigned ni = (unsigned)G.ni, n = ni * (unsigned)G.nj, stride = gridDim.x * 256u;
+    const T *__restrict__ src = U + (G.off - u_shift);
+    H *__restrict__ dst = packed + (G.poff - p_shift);
+    const long long pitch = G.pitch, plane = G.plane;
+    for (unsigned q0 = blockIdx.x * 256u + threadIdx.x; q0 < n; q0 += IO_PER * stride) {
+        T v[IO_PER][4];
+#pragma unroll
+        for (int e = 0; e < IO_PER; ++e) {
+            const unsigned q = q0 + e * stride;
+            if (q < n) {
+                const unsigned j = q / ni, i = q - j * ni;
+                const long long c = (long long)j * pitch + i;
+                for (int k = 0; k < 4; ++k) v[e][k] = src[c + k * plane];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < IO_PER; ++e) {
+            const unsigned q = q0 + e * stride;
+            if (q < n)
+                for (int k = 0; k < 4; ++k) dst[(long long)k * n + q] = (H)v[e][k];
+        }
     }
 }
 
@@ -1336,26 +1367,23 @@ int AblationLaunchers<T>::stage_occupancy(int muscl, int curv)
                 : StageVariant<T, false, false, true, true>::occupancy();
 }
 
-template <typename T>
-cudaError_t Launchers<T>::rate(const GridDev *grids, const GridCoef<T> *coef, int g_lo, int g_hi, const T *U,
-                               const T *vdx, const T *vdy, const uint8_t *solid, unsigned long long *rate, int curv,
-                               cudaStream_t s)
+// IO_PER cells per thread of a block of 256 for the largest grid (one pass over it), at most
+// 1024 blocks per grid.
+static inline int io_blocks(int max_cells)
 {
-    if (g_hi <= g_lo) return cudaSuccess;
-    dim3 grid(64, g_hi - g_lo);
-    if (curv) rate_kernel<T, true><<<grid, 256, 0, s>>>(grids, coef, g_lo, U, vdx, vdy, solid, rate);
-    else rate_kernel<T, false><<<grid, 256, 0, s>>>(grids, coef, g_lo, U, vdx, vdy, solid, rate);
-    return cudaGetLastError();
+    const int bx = (max_cells + 256 * IO_PER - 1) / (256 * IO_PER);
+    return bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
 }
 
 template <typename T, typename H>
 static cudaError_t launch_pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const H *packed, T *U,
-                               cudaStream_t s, long long p_shift)
+                               cudaStream_t s, long long p_shift, const RateOut<T> *ro)
 {
     if (g_hi <= g_lo) return cudaSuccess;
-    int bx = (max_cells + 255) / 256;
-    bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
-    pack_kernel<T, H><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, packed, U, p_shift);
+    const dim3 grid(io_blocks(max_cells), g_hi - g_lo);
+    if (!ro) pack_kernel<T, H, false, false><<<grid, 256, 0, s>>>(grids, g_lo, packed, U, p_shift, RateOut<T>());
+    else if (ro->curv) pack_kernel<T, H, true, true><<<grid, 256, 0, s>>>(grids, g_lo, packed, U, p_shift, *ro);
+    else pack_kernel<T, H, true, false><<<grid, 256, 0, s>>>(grids, g_lo, packed, U, p_shift, *ro);
     return cudaGetLastError();
 }
 
@@ -1364,23 +1392,22 @@ static cudaError_t launch_unpack(const GridDev *grids, int g_lo, int g_hi, int m
                                  cudaStream_t s, long long u_shift, long long p_shift)
 {
     if (g_hi <= g_lo) return cudaSuccess;
-    int bx = (max_cells + 255) / 256;
-    bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
-    unpack_kernel<T, H><<<dim3(bx, g_hi - g_lo), 256, 0, s>>>(grids, g_lo, U, packed, u_shift, p_shift);
+    unpack_kernel<T, H><<<dim3(io_blocks(max_cells), g_hi - g_lo), 256, 0, s>>>(grids, g_lo, U, packed, u_shift,
+                                                                                 p_shift);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launchers<T>::pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const double *packed, T *U,
-                               cudaStream_t s, long long p_shift)
+                               cudaStream_t s, long long p_shift, const RateOut<T> *ro)
 {
-    return launch_pack<T, double>(grids, g_lo, g_hi, max_cells, packed, U, s, p_shift);
+    return launch_pack<T, double>(grids, g_lo, g_hi, max_cells, packed, U, s, p_shift, ro);
 }
 template <typename T>
 cudaError_t Launchers<T>::pack(const GridDev *grids, int g_lo, int g_hi, int max_cells, const float *packed, T *U,
-                               cudaStream_t s, long long p_shift)
+                               cudaStream_t s, long long p_shift, const RateOut<T> *ro)
 {
-    return launch_pack<T, float>(grids, g_lo, g_hi, max_cells, packed, U, s, p_shift);
+    return launch_pack<T, float>(grids, g_lo, g_hi, max_cells, packed, U, s, p_shift, ro);
 }
 
 template <typename T>
