@@ -125,20 +125,37 @@ def test_largest_grid_sampled_parity():
     check_cells(spec, U0, U1, dt, cells, 1e-5)
 
 
+def _restart_workload(kind):
+    if kind == "warped_muscl":
+        spec = W.with_params(W.warped_periodic(48, amp=0.15), recon=2)
+        return [spec], [W.random_smooth_state(spec, seed=8, mach=0.7, amp=0.4)]
+    if kind == "step_solid":
+        spec, U = W.warped_step(96, 40)
+        return [spec], [U]
+    return W.batch(12, seed=17, ni_range=(20, 90), nj_range=(8, 70))
+
+
+@pytest.mark.parametrize("kind", ["warped_muscl", "step_solid", "batch"])
 @pytest.mark.parametrize("prec", [64, 32])
-def test_checkpoint_restart_is_bit_identical(prec):
-    spec = W.with_params(W.warped_periodic(48, amp=0.15), recon=2)
-    U = W.random_smooth_state(spec, seed=8, mach=0.7, amp=0.4)
-    with P().Batch([spec], precision=prec) as a:
-        a.set_state(U, 0)
+def test_checkpoint_restart_is_bit_identical(prec, kind):
+    """Stopping after 10 steps, reading the state back and loading it into a new handle gives
+    the continuous run's next 13 steps bit for bit. The first restarted step takes its dt from
+    the rate the state load computes while it packs the state; the continuous run takes it from
+    the third stage's epilogue: the two must agree to the bit (curvilinear MUSCL; the step with
+    a solid block, walls, inflow and outflow; a batch of ragged periodic grids)."""
+    specs, states = _restart_workload(kind)
+    with P().Batch(specs, precision=prec) as a:
+        a.set_states(states)
         a.step(0.5, nsteps=10)
-        U10 = a.get_state(0)
-        a.step(0.5, nsteps=13)
-        U23 = a.get_state(0)
-    with P().Batch([spec], precision=prec) as b:
-        b.set_state(U10, 0)
-        b.step(0.5, nsteps=13)
-        assert np.array_equal(b.get_state(0), U23)
+        U10 = a.get_states()
+        dt_a = a.step(0.5, nsteps=13, want_dt=True)
+        U23 = a.get_states()
+    with P().Batch(specs, precision=prec) as b:
+        b.set_states(U10)
+        dt_b = b.step(0.5, nsteps=13, want_dt=True)
+        for x, y in zip(b.get_states(), U23):
+            assert np.array_equal(x, y)
+    assert np.array_equal(dt_a, dt_b)
 
 
 @pytest.mark.parametrize("name", ["expansion", "near_vacuum", "strong"])

@@ -318,6 +318,29 @@ def test_step_host_matches_separate_calls(prec, cfg):
     assert np.array_equal(buf, ref)
 
 
+@pytest.mark.parametrize("count", [1, 2, 9, 10, 11, 25])
+def test_step_host_chunking_over_grid_counts(count):
+    """roeam_step_host_f32 cuts the batch into up to ten chunks of whole grids: with fewer grids
+    than chunks, as many as chunks, and more, it gives the state and time steps of
+    set_state + rk_step + get_state bit for bit (FP32 handle, float32 host arrays)."""
+    import torch
+    specs, states = W.batch(count, seed=400 + count, ni_range=(16, 120), nj_range=(8, 100))
+    packed = np.concatenate([s.ravel() for s in states]).astype(np.float32)
+    h_in = torch.from_numpy(packed.copy()).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    dt_a = np.zeros(count)
+    with P().Batch(specs, precision=32) as b:
+        P().roeam_step_host_f32(b.handle, 0.5, 0.0, 2, h_in, h_out, dt_a)
+        got = h_out.numpy().copy()
+    with P().Batch(specs, precision=32) as b:
+        P().roeam_set_state_f32(b.handle, -1, packed)
+        dt_b = b.step(0.5, nsteps=2, want_dt=True)
+        ref = np.empty_like(packed)
+        P().roeam_get_state_f32(b.handle, -1, ref)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(dt_a, dt_b)
+
+
 @pytest.mark.parametrize("cfg", TILE_CFGS)
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("shape", [(4, 4), (5, 7), (31, 4), (33, 5), (4, 65), (61, 6), (29, 129)])
