@@ -1,8 +1,8 @@
 // roeam3_api.cu — host implementation of the 3D C ABI declared in include/roeam3.h.
 //
 // Owns the device memory of a batch of 3D grids (pitched structure-of-arrays volumes, one per
-// conserved variable), builds the work units of the 3D stage kernel (30 x 6 columns of a plane
-// by a segment of planes), and drives the three fused stage launches of each SSP-RK3 step with
+// conserved variable), builds the work units of the 3D stage kernel (30 x 14 columns of a plane
+// in FP32, 30 x 6 in FP64, by a segment of planes), and drives the three fused stage launches of each SSP-RK3 step with
 // per-grid time steps read on the device.
 #include <cuda_runtime.h>
 
@@ -135,7 +135,8 @@ roeam_status upload_coef3(roeam3_grid *g, const roeam3_grid_desc *d)
     return ROEAM_OK;
 }
 
-// Work units: 30 x 6 columns of a plane (TILE3_X x TILE3_Y written cells) by a segment of
+// Work units: 30 x 14 columns of a plane in FP32, 30 x 6 in FP64 (TILE3_X x tile3_y<T>() written
+// cells) by a segment of
 // planes. The number of segments per column starts at about four units per resident CTA and is
 // then chosen, up to twice that, to fill the last round of units over the CTAs (all units cost
 // about the same): the 256^3 Taylor-Green vortex had 1548 units over 304 CTAs, a sixth round
@@ -146,6 +147,7 @@ roeam_status setup_units3(roeam3_grid *g, int num_sms)
     const int occ = g->precision == 32 ? Launchers3<float>::stage_occupancy(g->nscal)
                                        : Launchers3<double>::stage_occupancy(g->nscal);
     g->nblocks = std::max(1, occ * num_sms);
+    const int TILE3_Y = g->precision == 32 ? tile3_y<float>() : tile3_y<double>();
     long long columns = 0, nk_max = 1;
     for (const GridDev3 &G : g->hg) {
         columns += (long long)((G.ni + TILE3_X - 1) / TILE3_X) * ((G.nj + TILE3_Y - 1) / TILE3_Y);

@@ -32,13 +32,20 @@ struct GridCoef3 {
     T inflow[MAX_VARS3];
 };
 
-// Work-unit shape of the 3D stage kernel: a CTA of TY3 warps covers 32 columns (30 written)
-// by TY3 rows (TY3 - 2 written) and marches along z over a segment of planes.
-#ifndef ROEAM_TY3
-#define ROEAM_TY3 8
+// Work-unit shape of the 3D stage kernel: a CTA of ty3<T>() warps covers 32 columns (30
+// written) by ty3<T>() rows (two fewer written) and marches along z over a segment of planes.
+// FP32 takes 16-row tiles, one 512-thread CTA per SM at 128 registers (30 x 14 of its 32 x 16
+// cells written; 8-row tiles, two CTAs per SM, write 30 x 6 of 32 x 8 and measured 3.4 % slower
+// on the 256^3 Taylor-Green vortex); FP64, which needs up to 255 registers, 8-row tiles.
+#ifndef ROEAM_TY3_F32
+#define ROEAM_TY3_F32 16
 #endif
-constexpr int TY3 = ROEAM_TY3;
-constexpr int TILE3_X = 30, TILE3_Y = TY3 - 2;
+#ifndef ROEAM_TY3_F64
+#define ROEAM_TY3_F64 8
+#endif
+template <typename T> __host__ __device__ constexpr int ty3() { return sizeof(T) == 4 ? ROEAM_TY3_F32 : ROEAM_TY3_F64; }
+template <typename T> __host__ __device__ constexpr int tile3_y() { return ty3<T>() - 2; }
+constexpr int TILE3_X = 30;
 
 template <typename T>
 struct StageArgs3 {

@@ -2,9 +2,9 @@
 // passive scalars (the complete form of Eq. 85, the 9-face detector of Eq. 96), fused with the
 // residual and the SSP-RK3 stage update like the 2D kernels.
 //
-// Decomposition: a CTA of TY3 warps holds a 32 x TY3 tile of an (x, y) plane, lane = column,
-// warp = row (one halo column and row on each side), and marches along z over a segment of
-// planes. Each thread keeps its cell's primitives for planes k-1, k, k+1 in registers (the
+// Decomposition: a CTA of TY3 = ty3<T>() warps (16 in FP32, 8 in FP64) holds a 32 x TY3 tile of
+// an (x, y) plane, lane = column, warp = row (one halo column and row on each side), and marches
+// along z over a segment of planes. Each thread keeps its cell's primitives for planes k-1, k, k+1 in registers (the
 // z-faces and their detector values), exchanges plane k with its x-neighbours by shuffles and
 // with its y-neighbours through shared memory (double-buffered by plane parity, one block
 // barrier per plane: the row above's south flux of plane k is read after the barrier of
@@ -263,14 +263,15 @@ __device__ __forceinline__ T cell_rate3(const Prims3<T> &s, const GridCoef3<T> &
 // Shared-memory exchange of one plane: fields [9 + NS cell values][3 detector values][NV flux
 // values], each TY3 x 32, double-buffered by plane parity.
 template <typename T, int NS> struct Smem3 {
-    static constexpr int NC = 9 + NS, NP = 3, NV = 5 + NS, PER = (NC + NP + NV) * TY3 * 32;
+    static constexpr int NC = 9 + NS, NP = 3, NV = 5 + NS, PER = (NC + NP + NV) * ty3<T>() * 32;
     static __host__ __device__ constexpr size_t bytes() { return sizeof(T) * 2 * (size_t)PER; }
 };
 
-// FP32 with 8-warp CTAs: two CTAs per SM (128 registers).
+// FP32: 16-warp CTAs, one per SM (128 registers); FP64: 8-warp CTAs.
 template <typename T, int NS>
-__global__ void __launch_bounds__(32 * TY3, (sizeof(T) == 4 && TY3 <= 8) ? 2 : 1) stage3_kernel(const StageArgs3<T> a)
+__global__ void __launch_bounds__(32 * ty3<T>(), (sizeof(T) == 4 && ty3<T>() <= 8) ? 2 : 1) stage3_kernel(const StageArgs3<T> a)
 {
+    constexpr int TY3 = ty3<T>();
     using SM = Smem3<T, NS>;
     constexpr int NV = 5 + NS, NC = SM::NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -571,7 +572,7 @@ template <typename T, int NS> struct Stage3Variant {
         cudaError_t e = cudaFuncSetAttribute(stage3_kernel<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Smem3<T, NS>::bytes());
         if (e != cudaSuccess) return e;
-        stage3_kernel<T, NS><<<nblocks, 32 * TY3, Smem3<T, NS>::bytes(), s>>>(a);
+        stage3_kernel<T, NS><<<nblocks, 32 * ty3<T>(), Smem3<T, NS>::bytes(), s>>>(a);
         return cudaGetLastError();
     }
     static int occupancy()
@@ -579,7 +580,7 @@ template <typename T, int NS> struct Stage3Variant {
         cudaFuncSetAttribute(stage3_kernel<T, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Smem3<T, NS>::bytes());
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage3_kernel<T, NS>, 32 * TY3, Smem3<T, NS>::bytes()) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage3_kernel<T, NS>, 32 * ty3<T>(), Smem3<T, NS>::bytes()) !=
             cudaSuccess)
             return 1;
         return n > 0 ? n : 1;

@@ -42,9 +42,11 @@ def one_step3(spec, U, prec, cfl=0.5, presteps=0):
 
 
 CASES3 = {
-    # ragged tiles in x and y (30 x 6 written per tile), several z segments
+    # ragged tiles in x and y (30 x 14 written per FP32 tile, 30 x 6 per FP64 one), several z segments
     "periodic_ns0": lambda: (W.GridSpec3(ni=37, nj=15, nk=11, dx=0.05, dy=0.06, dz=0.07,
                                          params=W.SchemeParams(m_ref=0.4)), 1.2),
+    "periodic_ns0_tall": lambda: (W.GridSpec3(ni=34, nj=31, nk=6, dx=0.05, dy=0.045, dz=0.07,
+                                              params=W.SchemeParams(m_ref=0.6)), 1.1),
     "periodic_ns1_eps1": lambda: (W.GridSpec3(ni=31, nj=13, nk=9, dx=0.05, dy=0.05, dz=0.05, nscal=1,
                                               params=W.SchemeParams(m_ref=0.8, eps1=1)), 1.5),
     "bcs_ns2": lambda: (W.GridSpec3(ni=33, nj=14, nk=10, dx=0.05, dy=0.04, dz=0.06, nscal=2,
