@@ -119,12 +119,6 @@ __device__ __forceinline__ void roeam_flux3(const FS3<V, NS> &L, const FS3<V, NS
                                             int eps1, int xi_form, V F[5 + NS])
 {
     const V zero = splat<V>(0), one = splat<V>(1), half = splat<V>(S(0.5));
-    const V mL = L.r * L.un, mR = R.r * R.un;
-    const V F0c = mL + mR;
-    const V F1c = vfma(mL, L.un, vfma(mR, R.un, L.p + R.p));
-    const V F2c = vfma(mL, L.ut, mR * R.ut);
-    const V F3c = vfma(mL, L.uw, mR * R.uw);
-    const V F4c = vfma(mL, L.H, mR * R.H);
 
     const V w = rcp(L.sr + R.sr);
     const V rh = L.sr * R.sr;
@@ -145,11 +139,11 @@ __device__ __forceinline__ void roeam_flux3(const FS3<V, NS> &L, const FS3<V, NS
     const V fM8 = pow8(fM), fMb8 = pow8(fMb);
     const V dp = R.p - L.p;
 
-    const V br = sel(lt(aU, ch), splat<V>(2), sel(eq(aU, ch), one, zero));
+    const V br = bracket(aU, ch);
     const V Up = vmax(vfma(splat<V>(S(-0.25)) * fMb * br, vmax(du, zero), aU), zero);   // du <= 0 leaves |U|
 
-    const V xfac = xi_form ? one : one - fMb8;
-    V xi = vmax(vfma(xfac * half, du, vabs(half * (L.un + R.un))), zero);
+    const V xfh = xi_form ? half : vfma(splat<V>(S(-0.5)), fMb8, half);   // [1 - f^8(Mbar)] / 2
+    V xi = vmax(vfma(xfh, du, vabs(half * (L.un + R.un))), zero);
     if (eps1) {
         const V dq = sqrt0(dq2);
         const auto big = ge(dq, splat<V>(K.rr_thr));
@@ -165,26 +159,27 @@ __device__ __forceinline__ void roeam_flux3(const FS3<V, NS> &L, const FS3<V, NS
     const V pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmax(ch - Up, zero) * rh * du);
     const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
     const V om = one - th;
-    const V X = vfma(splat<V>(4) * c2h, th, om * om * uh * uh);
+    const V ou = om * uh;
+    const V X = vfma(ou, ou, (splat<V>(4) * c2h) * th);
     const V rX = rsq(X);
     const V ct = half * X * rX;
-    const V Ut = half * (one + th) * uh;
-    const V term = vfma(om, Up - aU * rX * vmin(vabs(Ut), ct), vmax(ct - Up, zero));
-    const V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
+    const V aUt = vfma(half, th, half) * aU;   // |U~| = (1 + theta) |U| / 2
+    const V term = vfma(om, Up - aU * rX * vmin(aUt, ct), vmax(ct - Up, zero));
+    const V nA = s1 * (fM8 - one) * term * dp * chi * chi * rcp(th);   // -rho delta U_p
     const V dUu = half * smc * du;
 
-    const V QL2 = L.r * L.ut, QR2 = R.r * R.ut, QL3 = L.r * L.uw, QR3 = R.r * R.uw;
-    const V QL4 = L.r * L.H, QR4 = R.r * R.H;
-    F[0] = F0c - vfma(xi, R.r - L.r, vfma(dUu, R.r + L.r, A));
-    F[1] = F1c - vfma(xi, mR - mL, vfma(dUu, mR + mL, vfma(A, uh, pp)));
-    F[2] = F2c - vfma(xi, QR2 - QL2, vfma(dUu, QR2 + QL2, A * vh));
-    F[3] = F3c - vfma(xi, QR3 - QL3, vfma(dUu, QR3 + QL3, A * wh));
-    F[4] = F4c - vfma(xi, QR4 - QL4, vfma(dUu, QR4 + QL4, A * Hh));
+    // Eq. 85 per side (as in roeam_flux2): rho_side (U_side +- xi - dUu) times the side's
+    // (1, U, V, W, H, k), plus the pressure and delta U_p terms.
+    const V gL = L.r * (L.un + (xi - dUu)), gR = R.r * (R.un - (xi + dUu));
+    F[0] = (gL + gR) + nA;
+    F[1] = vfma(gL, L.un, vfma(gR, R.un, vfma(nA, uh, L.p + R.p) - pp));
+    F[2] = vfma(gL, L.ut, vfma(gR, R.ut, nA * vh));
+    F[3] = vfma(gL, L.uw, vfma(gR, R.uw, nA * wh));
+    F[4] = vfma(gL, L.H, vfma(gR, R.H, nA * Hh));
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const V QLk = L.r * L.k[s], QRk = R.r * R.k[s];
         const V kh = vfma(L.sr, L.k[s], R.sr * R.k[s]) * w;
-        F[5 + s] = vfma(mL, L.k[s], mR * R.k[s]) - vfma(xi, QRk - QLk, vfma(dUu, QRk + QLk, A * kh));
+        F[5 + s] = vfma(gL, L.k[s], vfma(gR, R.k[s], nA * kh));
     }
 }
 
@@ -224,7 +219,7 @@ __device__ __forceinline__ void faces3_xy(const C3<float, NS> &Lx, const C3<floa
 
 template <typename T> __device__ __forceinline__ T min9(T a, T b, T c, T d, T e, T f, T g, T h, T i)
 {
-    return vmin(vmin(vmin(a, b), vmin(c, d)), vmin(vmin(e, f), vmin(vmin(g, h), i)));
+    return fmn3(fmn3(a, b, c), fmn3(d, e, f), fmn3(g, h, i));   // (positive ratios, never NaN)
 }
 
 // Velocity, |q|^2 and pressure of a conserved 3D state, with explicit rounding (the stage

@@ -56,6 +56,24 @@ template <typename T> __device__ __forceinline__ T vmin(T a, T b) { return a < b
 template <typename T> __device__ __forceinline__ T vmax(T a, T b) { return a > b ? a : b; }
 __device__ __forceinline__ V2 vmin(V2 a, V2 b) { return mk2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y)); }
 __device__ __forceinline__ V2 vmax(V2 a, V2 b) { return mk2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+// Minimum and maximum as single instructions (the a < b ? a : b forms above must keep their
+// NaN and signed-zero behaviour, which costs a compare and a select). For the positive ratios
+// of the detector, whose operands are never NaN, the results are the same; the three-operand
+// minimum is one instruction on sm_100-class GPUs.
+__device__ __forceinline__ float fmn(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double fmn(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float fmx(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double fmx(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float fmn3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double fmn3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+// 1 where a < b (a <= b), else 0, as one instruction each (PTX set).
+__device__ __forceinline__ float setlt(float a, float b) { float r; asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r; }
+__device__ __forceinline__ float setle(float a, float b) { float r; asm("set.le.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r; }
 __device__ __forceinline__ float vabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double vabs(double a) { return fabs(a); }
 __device__ __forceinline__ V2 vabs(V2 a) { return mk2(fabsf(a.v.x), fabsf(a.v.y)); }
@@ -193,6 +211,15 @@ __device__ __forceinline__ FS<V> side_from_prims(V r, V un, V ut, V p, const Gri
     return s;
 }
 
+// The bracket sgn(U + c) - sgn(U - c) of Eq. 92 for |U| and c >= 0: 2 for |U| < c, 1 for
+// |U| = c, 0 above (in FP32 as the sum of two set instructions).
+__device__ __forceinline__ float bracket(float aU, float c) { return setlt(aU, c) + setle(aU, c); }
+__device__ __forceinline__ double bracket(double aU, double c) { return aU < c ? 2.0 : (aU == c ? 1.0 : 0.0); }
+__device__ __forceinline__ V2 bracket(V2 aU, V2 c)
+{
+    return mk2(setlt(aU.v.x, c.v.x), setlt(aU.v.y, c.v.y)) + mk2(setle(aU.v.x, c.v.x), setle(aU.v.y, c.v.y));
+}
+
 // Ablation variants of the flux (the schemes Section 7 compares with), read per grid by the
 // ablation kernels only: scheme 1 is classical Roe (Eq. 7 with Eqs. 8-12, entropy fix of
 // Eqs. 114-115 with GridCoef::harten); for Roe-AM, dup_mode 1 sets delta U_p = 0 and 2 takes
@@ -211,11 +238,6 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
                                             int xi_form, V F[4], const Variant &var = Variant())
 {
     const V zero = splat<V>(0), one = splat<V>(1), half = splat<V>(S(0.5));
-    const V mL = L.r * L.un, mR = R.r * R.un;
-    const V F0c = mL + mR;
-    const V F1c = vfma(mL, L.un, vfma(mR, R.un, L.p + R.p));
-    const V F2c = vfma(mL, L.ut, mR * R.ut);
-    const V F3c = vfma(mL, L.H, mR * R.H);
 
     // Roe averages; c^2 in the sum-of-positives form (no cancellation at high Mach).
     const V w = rcp(L.sr + R.sr);
@@ -225,7 +247,7 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     const V Hh = vfma(L.sr, L.H, R.sr * R.H) * w;
     const V du = R.un - L.un, dv = R.ut - L.ut;
     const V dq2 = vfma(du, du, dv * dv);
-    const V c2h = vfma(vfma(L.sr, L.c2, R.sr * R.c2), w, splat<V>(K.hgm1) * rh * w * w * dq2);
+    const V c2h = vfma(splat<V>(K.hgm1) * rh * w, dq2, vfma(L.sr, L.c2, R.sr * R.c2)) * w;
     const V chi = rsq(c2h);
     const V ch = c2h * chi;
     const V aU = vabs(uh);
@@ -245,6 +267,11 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
                 l4 = sel(lt(l4, hh), half * vfma(l4 * l4, hi, hh), l4);
                 l5 = sel(lt(l5, hh), half * vfma(l5 * l5, hi, hh), l5);
             }
+            const V mL = L.r * L.un, mR = R.r * R.un;
+            const V F0c = mL + mR;
+            const V F1c = vfma(mL, L.un, vfma(mR, R.un, L.p + R.p));
+            const V F2c = vfma(mL, L.ut, mR * R.ut);
+            const V F3c = vfma(mL, L.H, mR * R.H);
             const V dp = R.p - L.p;
             const V spp = vfma(half, l5 + l4, -l1), smm = half * (l5 - l4);
             const V pp = vfma(spp * rh, du, smm * dp * chi);
@@ -265,15 +292,16 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     const V dp = R.p - L.p;
 
     // |U|': the bracket sgn(U + c) - sgn(U - c) is 2 for |U| < c, 1 for |U| = c, 0 above.
-    const V br = sel(lt(aU, ch), splat<V>(2), sel(eq(aU, ch), one, zero));
+    const V br = bracket(aU, ch);
     // (du <= 0 leaves |U|: the correction is applied to max(du, 0))
     V Up = vmax(vfma(splat<V>(S(-0.25)) * fMb * br, vmax(du, zero), aU), zero);
     if constexpr (ABL) {
         if (!var.ufix) Up = aU;
     }
 
-    const V xfac = xi_form ? one : one - fMb8;
-    V xi = vmax(vfma(xfac * half, du, vabs(half * (L.un + R.un))), zero);
+    // xi's factor [1 - f^8(Mbar)] / 2 on dU (1/2 with xi_form = 1)
+    const V xfh = xi_form ? half : vfma(splat<V>(S(-0.5)), fMb8, half);
+    V xi = vmax(vfma(xfh, du, vabs(half * (L.un + R.un))), zero);
     if (eps1) {
         // Rotated-Riemann estimate in the face frame (n = (1, 0)): n1 = dq / |dq| unless
         // |dq| < 1e-5 U_ref; |alpha1 U1| + |alpha2 U2| with the unit n2 perpendicular to n1.
@@ -295,24 +323,31 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     const V pp = vfma(smc, dp, vfma(s1, fM, one - s1) * vmax(ch - Up, zero) * rh * du);
     const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
     const V om = one - th;
-    const V X = vfma(splat<V>(4) * c2h, th, om * om * uh * uh);
+    const V ou = om * uh;
+    const V X = vfma(ou, ou, (splat<V>(4) * c2h) * th);
     const V rX = rsq(X);           // 1 / (2 c~)
     const V ct = half * X * rX;    // c~
-    const V Ut = half * (one + th) * uh;
-    // U sgn(U~) min(|U~|, c~) = |U| min(|U~|, c~): U~ = (1 + theta) U / 2 has the sign of U
-    const V term = vfma(om, vfnma(aU * rX, vmin(vabs(Ut), ct), Up), vmax(ct - Up, zero));
-    V A = s1 * (one - fM8) * term * dp * chi * chi * rcp(th);
+    // |U~| = (1 + theta) |U| / 2, and U sgn(U~) min(|U~|, c~) = |U| min(|U~|, c~): U~ has the
+    // sign of U
+    const V aUt = vfma(half, th, half) * aU;
+    const V term = vfma(om, vfnma(aU * rX, vmin(aUt, ct), Up), vmax(ct - Up, zero));
+    // -rho delta U_p (the sign is taken into the factor 1 - f^8(M))
+    V nA = s1 * (fM8 - one) * term * dp * chi * chi * rcp(th);
     if constexpr (ABL) {
-        if (var.dup_mode == 1) A = zero;
-        else if (var.dup_mode == 2) A = vmax(ch - aU, zero) * dp * chi * chi;   // rho x Eq. 17
+        if (var.dup_mode == 1) nA = zero;
+        else if (var.dup_mode == 2) nA = -(vmax(ch - aU, zero) * dp * chi * chi);   // rho x Eq. 17
     }
     const V dUu = half * smc * du;
 
-    const V QL2 = L.r * L.ut, QR2 = R.r * R.ut, QL3 = L.r * L.H, QR3 = R.r * R.H;
-    F[0] = F0c - vfma(xi, R.r - L.r, vfma(dUu, R.r + L.r, A));
-    F[1] = F1c - vfma(xi, mR - mL, vfma(dUu, mR + mL, vfma(A, uh, pp)));
-    F[2] = F2c - vfma(xi, QR2 - QL2, vfma(dUu, QR2 + QL2, A * vh));
-    F[3] = F3c - vfma(xi, QR3 - QL3, vfma(dUu, QR3 + QL3, A * Hh));
+    // Eq. 85 assembled per side: the central flux, the xi and delta U_u terms of a side carry
+    // the same factor rho_side (U_side + xi - dUu) or rho_side (U_side - xi - dUu) times the
+    // side's (1, U, V, H), so each component is two products of that factor plus the
+    // pressure and delta U_p terms.
+    const V gL = L.r * (L.un + (xi - dUu)), gR = R.r * (R.un - (xi + dUu));
+    F[0] = (gL + gR) + nA;
+    F[1] = vfma(gL, L.un, vfma(gR, R.un, vfma(nA, uh, L.p + R.p) - pp));
+    F[2] = vfma(gL, L.ut, vfma(gR, R.ut, nA * vh));
+    F[3] = vfma(gL, L.H, vfma(gR, R.H, nA * Hh));
 }
 
 // ------------------------------------------------------------------ geometry
@@ -426,9 +461,9 @@ template <typename T> __device__ __forceinline__ T ratio_P(T r0, T p0, T r1, T p
 {
     // Eq. 97; in FP32 each ratio is the smaller value times the reciprocal of the larger
     if constexpr (sizeof(T) == 4)
-        return vmin(vmin(p0, p1) * rcp(vmax(p0, p1)), vmin(r0, r1) * rcp(vmax(r0, r1)));
+        return fmn(fmn(p0, p1) * rcp(fmx(p0, p1)), fmn(r0, r1) * rcp(fmx(r0, r1)));
     else
-        return vmin(vmin(p0, p1) / vmax(p0, p1), vmin(r0, r1) / vmax(r0, r1));
+        return fmn(fmn(p0, p1) / fmx(p0, p1), fmn(r0, r1) / fmx(r0, r1));
 }
 
 // MUSCL limited slope: minmod(a, b) = (sgn a + sgn b)/2 min(|a|, |b|); van Leer
@@ -600,21 +635,26 @@ __device__ __forceinline__ void faces_packed(const Face<float> &fx, const Face<f
     }
     V2 G2[4];
     roeam_flux2(L, R, mk2(fx.s1, fy.s1), K, eps1, xi_form, G2);
-    const float hx = 0.5f * fx.len, hy = 0.5f * fy.len;
-    Fx[0] = hx * G2[0].v.x;
-    Fx[3] = hx * G2[3].v.x;
-    Fy[0] = hy * G2[0].v.y;
-    Fy[3] = hy * G2[3].v.y;
     if constexpr (CURV) {
+        const float hx = 0.5f * fx.len, hy = 0.5f * fy.len;
+        Fx[0] = hx * G2[0].v.x;
+        Fx[3] = hx * G2[3].v.x;
+        Fy[0] = hy * G2[0].v.y;
+        Fy[3] = hy * G2[3].v.y;
         Fx[1] = hx * vfnma(fx.ny, G2[2].v.x, fx.nx * G2[1].v.x);
         Fx[2] = hx * vfma(fx.ny, G2[1].v.x, fx.nx * G2[2].v.x);
         Fy[1] = hy * vfnma(fy.ny, G2[2].v.y, fy.nx * G2[1].v.y);
         Fy[2] = hy * vfma(fy.ny, G2[1].v.y, fy.nx * G2[2].v.y);
     } else {
-        Fx[1] = hx * G2[1].v.x;
-        Fx[2] = hx * G2[2].v.x;
-        Fy[1] = hy * G2[2].v.y;
-        Fy[2] = hy * G2[1].v.y;
+        // (twice the flux: the residual applies the half lengths)
+        Fx[0] = G2[0].v.x;
+        Fx[1] = G2[1].v.x;
+        Fx[2] = G2[2].v.x;
+        Fx[3] = G2[3].v.x;
+        Fy[0] = G2[0].v.y;
+        Fy[1] = G2[2].v.y;
+        Fy[2] = G2[1].v.y;
+        Fy[3] = G2[3].v.y;
     }
 }
 
@@ -849,6 +889,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         const int isrc = resolve_index(i, ni, R.bcW, R.bcE, kx);
         const bool icol = i >= 0 && i < ni;
         const bool out_lane = lane >= H && lane < H + WIDTH && icol;
+        const T rxy = K.dy / K.dx, cy = T(0.5) * K.dx * K.Vi;   // Cartesian residual weights
         T dt = T(0);
         if (a.mode == MODE_STAGE) {
             if (a.dt_fixed_t > T(0)) dt = a.dt_fixed_t;
@@ -949,8 +990,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 // Eq. 96 in 2D: the face and the transverse faces of both cells.
                 const T pym_l = shup(Py[H - 1], 1), pyp_l = shup(Py[H], 1);
                 const T pxm_r = shdn(Px[H - 1], 1), px0_r = shdn(Px[H], 1);
-                T ax = vmin(vmin(Px[H], pym_l), vmin(vmin(pyp_l, Py[H - 1]), Py[H]));
-                T ay = vmin(vmin(Py[H - 1], Px[H - 1]), vmin(vmin(pxm_r, Px[H]), px0_r));
+                T ax = fmn3(fmn3(Px[H], pym_l, pyp_l), Py[H - 1], Py[H]);
+                T ay = fmn3(fmn3(Py[H - 1], Px[H - 1], pxm_r), Px[H], px0_r);
                 if constexpr (PACKED) {
                     const V2 s1 = detector_of(mk2(ax, ay));
                     fx.s1 = s1.v.x; fy.s1 = s1.v.y;
@@ -976,8 +1017,10 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     fy.nAmx = fy.nBpx = fy.nx; fy.nAmy = fy.nBpy = fy.ny;
                 }   // (reconstructing: set on the scalar path, the only one that reads them)
             } else {
-                fx.nx = T(1); fx.ny = T(0); fx.len = K.dy;
-                fy.nx = T(0); fy.ny = T(1); fy.len = K.dx;
+                // (Cartesian faces leave the length out: len = 2 makes the face's factor
+                //  len / 2 one, and the residual applies dy / 2 and dx / 2 per direction)
+                fx.nx = T(1); fx.ny = T(0); fx.len = T(2);
+                fy.nx = T(0); fy.ny = T(1); fy.len = T(2);
                 fx.nAmx = fx.nBpx = T(1); fx.nAmy = fx.nBpy = T(0);
                 fy.nAmx = fy.nBpx = T(0); fy.nAmy = fy.nBpy = T(1);
             }
@@ -1056,9 +1099,13 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 }
                 if (out_lane) {
                     const bool solid = WALLS && (Wn[H - 1].fl & 1);
-                    const T Vi = CURV ? rcp(cg.V) : K.Vi;
                     T Rs[4];
-                    for (int k = 0; k < 4; ++k) Rs[k] = solid ? T(0) : (acc[k] - Fs[k]) * Vi;
+                    if constexpr (CURV) {
+                        const T Vi = rcp(cg.V);
+                        for (int k = 0; k < 4; ++k) Rs[k] = solid ? T(0) : (acc[k] - Fs[k]) * Vi;
+                    } else {
+                        for (int k = 0; k < 4; ++k) Rs[k] = solid ? T(0) : (acc[k] - Fs[k]) * cy;
+                    }
                     const int x = (j - 1) * R.pitch + i;
                     if (stage_mode) {
                         T out[4];
@@ -1111,18 +1158,25 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
             }
             if (j == j1) break;
             for (int k = 0; k < 4; ++k) Un[k] = Un_next[k];
-            for (int k = 0; k < 4; ++k) acc[k] = Fw[k] - shdn(Fw[k], 1) + Fs[k];
+            // (curvilinear faces carry their lengths; Cartesian ones twice the flux: the x-face
+            //  difference is weighted by dy / dx here and the sum scaled by 1 / (2 dy) above,
+            //  so that equal fluxes on opposite faces cancel exactly)
+            if constexpr (CURV) {
+                for (int k = 0; k < 4; ++k) acc[k] = Fw[k] - shdn(Fw[k], 1) + Fs[k];
+            } else {
+                for (int k = 0; k < 4; ++k) acc[k] = vfma(Fw[k] - shdn(Fw[k], 1), rxy, Fs[k]);
+            }
 
             // ---- advance the window: row j+2 enters from the prefetch
             for (int w = 0; w < NW - 1; ++w) { Wn[w] = Wn[w + 1]; Px[w] = Px[w + 1]; }
             for (int w = 0; w < NW - 2; ++w) Py[w] = Py[w + 1];
-            finish_cell<T, MUSCL, CURV, WALLS, ABL>(R, K, i, isrc, kx, j + 2, pend, Wn[NW - 1]);
+            finish_cell<T, MUSCL, CURV, WALLS, ABL>(R, K, i, isrc, kx, j + NW - H, pend, Wn[NW - 1]);
             Px[NW - 1] = px_of(Wn[NW - 1]);
             Py[NW - 2] = py_of(Wn[NW - 2], Wn[NW - 1]);
-            issue_cell<T, WALLS && !ABL, MUSCL>(R, isrc, kx, j + 3, pend);
+            issue_cell<T, WALLS && !ABL, MUSCL>(R, isrc, kx, j + NW - H + 1, pend);
             if constexpr (CURV) {
                 for (int v = 0; v < NV - 1; ++v) { vX[v] = vX[v + 1]; vY[v] = vY[v + 1]; }
-                vload(j + 3, vX[NV - 1], vY[NV - 1]);
+                vload(j + NV - 1, vX[NV - 1], vY[NV - 1]);
             }
         }
         if (a.want_rate) {
