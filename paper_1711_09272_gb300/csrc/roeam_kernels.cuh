@@ -1099,13 +1099,11 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 }
                 if (out_lane) {
                     const bool solid = WALLS && (Wn[H - 1].fl & 1);
-                    T Rs[4];
-                    if constexpr (CURV) {
-                        const T Vi = rcp(cg.V);
-                        for (int k = 0; k < 4; ++k) Rs[k] = solid ? T(0) : (acc[k] - Fs[k]) * Vi;
-                    } else {
-                        for (int k = 0; k < 4; ++k) Rs[k] = solid ? T(0) : (acc[k] - Fs[k]) * cy;
-                    }
+                    // R = D sc: the face sum D and its scale (1 / V, or 1 / (2 dy) for Cartesian
+                    // faces); a stage applies dt sc to D in one product
+                    T D[4];
+                    for (int k = 0; k < 4; ++k) D[k] = solid ? T(0) : acc[k] - Fs[k];
+                    const T sc = CURV ? rcp(cg.V) : cy;
                     const int x = (j - 1) * R.pitch + i;
                     if (stage_mode) {
                         T out[4];
@@ -1118,7 +1116,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                             // (mostly an L1 hit)
                             const T uk = (!MUSCL && !WALLS && sizeof(T) == 4) ? Uw[k]
                                                             : ((MUSCL && CURV) ? Uk[k] : __ldg(DBG_LD(R, DB_SRC, R.src + x + k * R.plane)));
-                            const T upd = vfma(dt, Rs[k], uk);
+                            const T upd = vfma(dt * sc, D[k], uk);
                             out[k] = combine ? vfma(a.alpha, Un[k], a.beta * upd) : upd;
                         }
                         for (int k = 0; k < 4; ++k)
@@ -1146,10 +1144,10 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                         }
                     } else if (a.mode == MODE_RESIDUAL) {
                         for (int k = 0; k < 4; ++k)
-                            if (DBG_ST(R, DB_DST, R.dst + (x + k * R.plane))) R.dst[x + k * R.plane] = Rs[k];
+                            if (DBG_ST(R, DB_DST, R.dst + (x + k * R.plane))) R.dst[x + k * R.plane] = D[k] * sc;
                     } else if (!solid) {
                         for (int k = 0; k < 4; ++k) {
-                            const double rk = (double)Rs[k];
+                            const double rk = (double)(D[k] * sc);
                             acc_s[k] = fma(rk, rk, acc_s[k]);
                             acc_m[k] = fmax(acc_m[k], fabs(rk));
                         }
