@@ -140,10 +140,10 @@ __device__ __forceinline__ void roeam_flux3(const FS3<V, NS> &L, const FS3<V, NS
     const V dp = R.p - L.p;
 
     const V br = bracket(aU, ch);
-    const V Up = vmax(vfma(splat<V>(S(-0.25)) * fMb * br, vmax(du, zero), aU), zero);   // du <= 0 leaves |U|
+    const V Up = vmx(vfma(splat<V>(S(-0.25)) * fMb * br, vmx(du, zero), aU), zero);   // du <= 0 leaves |U|
 
     const V xfh = xi_form ? half : vfma(splat<V>(S(-0.5)), fMb8, half);   // [1 - f^8(Mbar)] / 2
-    V xi = vmax(vfma(xfh, du, vabs(half * (L.un + R.un))), zero);
+    V xi = vmx(vfma(xfh, du, vabs(half * (L.un + R.un))), zero);
     if (eps1) {
         const V dq = sqrt0(dq2);
         const auto big = ge(dq, splat<V>(K.rr_thr));
@@ -151,20 +151,20 @@ __device__ __forceinline__ void roeam_flux3(const FS3<V, NS> &L, const FS3<V, NS
         const V n1x = sel(big, du * dqi, one);
         const V U1 = sel(big, vfma(du, uh, vfma(dv, vh, dw * wh)) * dqi, uh);
         const V frr = vabs(n1x * U1) + vabs(vfma(-n1x, U1, uh));
-        xi = vmax(xi, (one - fMb8) * fM8 * vmin(splat<V>(K.eps2) * ch, frr));
+        xi = vmx(xi, (one - fMb8) * fM8 * vmn(splat<V>(K.eps2) * ch, frr));
     }
 
-    const V mn = vmin(Up, ch);
+    const V mn = vmn(Up, ch);
     const V smc = vcopysign(mn, uh) * chi;
-    const V pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmax(ch - Up, zero) * rh * du);
-    const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
+    const V pp = vfma(smc, dp, (one - s1 + s1 * fM) * vmx(ch - Up, zero) * rh * du);
+    const V th = vmn(vmx(splat<V>(K.mr2), M * M), one);
     const V om = one - th;
     const V ou = om * uh;
     const V X = vfma(ou, ou, (splat<V>(4) * c2h) * th);
     const V rX = rsq(X);
     const V ct = half * X * rX;
     const V aUt = vfma(half, th, half) * aU;   // |U~| = (1 + theta) |U| / 2
-    const V term = vfma(om, Up - aU * rX * vmin(aUt, ct), vmax(ct - Up, zero));
+    const V term = vfma(om, Up - aU * rX * vmn(aUt, ct), vmx(ct - Up, zero));
     const V nA = s1 * (fM8 - one) * term * dp * chi * chi * rcp(th);   // -rho delta U_p
     const V dUu = half * smc * du;
 

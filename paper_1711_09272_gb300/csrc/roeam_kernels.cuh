@@ -71,6 +71,14 @@ __device__ __forceinline__ float fmn3(float a, float b, float c)
     return r;
 }
 __device__ __forceinline__ double fmn3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+// Minimum and maximum inside the flux, whose operands are finite: single instructions for
+// every operand type (the V2 forms above already are).
+__device__ __forceinline__ float vmn(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmn(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ V2 vmn(V2 a, V2 b) { return vmin(a, b); }
+__device__ __forceinline__ float vmx(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmx(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ V2 vmx(V2 a, V2 b) { return vmax(a, b); }
 // 1 where a < b (a <= b), else 0, as one instruction each (PTX set).
 __device__ __forceinline__ float setlt(float a, float b) { float r; asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r; }
 __device__ __forceinline__ float setle(float a, float b) { float r; asm("set.le.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r; }
@@ -163,11 +171,11 @@ template <typename V> __device__ __forceinline__ V pow8(V a) { V a2 = a * a, a4 
 template <typename V> __device__ __forceinline__ V fmach(V phi)
 {
     const V one = splat<V>(1);
-    const V p = vmin(phi, splat<V>(2));
+    const V p = vmn(phi, splat<V>(2));
     const V t = vfnma(p, p, one);
     const V s = vfma(t, t, splat<V>(4));
     const V q = vfma(p, p, one);
-    return vmin(p * s * rsq(s * q * q), one);
+    return vmn(p * s * rsq(s * q * q), one);
 }
 
 // Eq. 95 (with P values of Eq. 97 already reduced to their minimum a by Eq. 96). The
@@ -179,7 +187,7 @@ template <typename V> __device__ __forceinline__ V detector_of(V a)
     const V t = vfnma(a, a, one);
     const V s = vfma(t, t, splat<V>(4));
     const V q = vfma(a, a, one);
-    const V f = vmin(a * s * rsq(s * q * q), one);
+    const V f = vmn(a * s * rsq(s * q * q), one);
     return sel(ge(a, one), one, pow8(f));
 }
 
@@ -260,7 +268,7 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
             // acts on Delta(rho E) = Delta(rho H) - Delta p and the pressure vector carries U
             // in its energy slot.
             V l1 = aU, l4 = vabs(uh - ch), l5 = vabs(uh + ch);
-            const V hh = splat<V>(K.harten) * vmax(l1, vmax(l4, l5));
+            const V hh = splat<V>(K.harten) * vmx(l1, vmx(l4, l5));
             if (gt(hh, zero)) {
                 const V hi = rcp(hh);
                 l1 = sel(lt(l1, hh), half * vfma(l1 * l1, hi, hh), l1);
@@ -294,14 +302,14 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     // |U|': the bracket sgn(U + c) - sgn(U - c) is 2 for |U| < c, 1 for |U| = c, 0 above.
     const V br = bracket(aU, ch);
     // (du <= 0 leaves |U|: the correction is applied to max(du, 0))
-    V Up = vmax(vfma(splat<V>(S(-0.25)) * fMb * br, vmax(du, zero), aU), zero);
+    V Up = vmx(vfma(splat<V>(S(-0.25)) * fMb * br, vmx(du, zero), aU), zero);
     if constexpr (ABL) {
         if (!var.ufix) Up = aU;
     }
 
     // xi's factor [1 - f^8(Mbar)] / 2 on dU (1/2 with xi_form = 1)
     const V xfh = xi_form ? half : vfma(splat<V>(S(-0.5)), fMb8, half);
-    V xi = vmax(vfma(xfh, du, vabs(half * (L.un + R.un))), zero);
+    V xi = vmx(vfma(xfh, du, vabs(half * (L.un + R.un))), zero);
     if (eps1) {
         // Rotated-Riemann estimate in the face frame (n = (1, 0)): n1 = dq / |dq| unless
         // |dq| < 1e-5 U_ref; |alpha1 U1| + |alpha2 U2| with the unit n2 perpendicular to n1.
@@ -310,7 +318,7 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
         const V dqi = rcp(sel(big, dq, one));
         const V n1x = sel(big, du * dqi, one), n1y = sel(big, dv * dqi, zero);
         const V frr = vabs(n1x * vfma(n1x, uh, n1y * vh)) + vabs(n1y * (vfma(n1x, vh, -(n1y * uh))));
-        xi = vmax(xi, (one - fMb8) * fM8 * vmin(splat<V>(K.eps2) * ch, frr));
+        xi = vmx(xi, (one - fMb8) * fM8 * vmn(splat<V>(K.eps2) * ch, frr));
     }
     if constexpr (ABL) {
         if (var.xi_roe) xi = aU;
@@ -318,10 +326,10 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
 
     // sgn(U) min(|U|', c): min(|U|', c) = 0 whenever U = 0 (then |U|' = 0), so the sign can
     // be copied onto it
-    const V mn = vmin(Up, ch);
+    const V mn = vmn(Up, ch);
     const V smc = vcopysign(mn, uh) * chi;
-    const V pp = vfma(smc, dp, vfma(s1, fM, one - s1) * vmax(ch - Up, zero) * rh * du);
-    const V th = vmin(vmax(splat<V>(K.mr2), M * M), one);
+    const V pp = vfma(smc, dp, vfma(s1, fM, one - s1) * vmx(ch - Up, zero) * rh * du);
+    const V th = vmn(vmx(splat<V>(K.mr2), M * M), one);
     const V om = one - th;
     const V ou = om * uh;
     const V X = vfma(ou, ou, (splat<V>(4) * c2h) * th);
@@ -330,12 +338,12 @@ __device__ __forceinline__ void roeam_flux2(const FS<V> &L, const FS<V> &R, V s1
     // |U~| = (1 + theta) |U| / 2, and U sgn(U~) min(|U~|, c~) = |U| min(|U~|, c~): U~ has the
     // sign of U
     const V aUt = vfma(half, th, half) * aU;
-    const V term = vfma(om, vfnma(aU * rX, vmin(aUt, ct), Up), vmax(ct - Up, zero));
+    const V term = vfma(om, vfnma(aU * rX, vmn(aUt, ct), Up), vmx(ct - Up, zero));
     // -rho delta U_p (the sign is taken into the factor 1 - f^8(M))
     V nA = s1 * (fM8 - one) * term * dp * chi * chi * rcp(th);
     if constexpr (ABL) {
         if (var.dup_mode == 1) nA = zero;
-        else if (var.dup_mode == 2) nA = -(vmax(ch - aU, zero) * dp * chi * chi);   // rho x Eq. 17
+        else if (var.dup_mode == 2) nA = -(vmx(ch - aU, zero) * dp * chi * chi);   // rho x Eq. 17
     }
     const V dUu = half * smc * du;
 
