@@ -300,8 +300,17 @@ def warped_step_speed(P, torch, steps=20):
     v = spec.ncells * 3 / (ms * 1e-3) / 1e9
     peak, kind = peaks()
     rec = traffic_record("stage_kernel_curvilinear_record.json")
+    # the FP64 CPU oracle on the same workload at 512 x 512 (one SSP-RK3 step, one thread)
+    import oracle
+    oracle.build()
+    s2, U2 = W.warped_step(512, 512)
+    t0 = time.perf_counter()
+    oracle.OracleGrid(s2).step(U2, cfl=0.5)
+    t_orc = time.perf_counter() - t0
     return {"workload": "warped step 4096x4096 FP32, MUSCL van Leer, solid block, walls/inflow/outflow",
             "gcell_updates_per_s_per_stage": v, "ms_per_step": ms,
+            "cpu_oracle": {"value": s2.ncells * 3 / t_orc / 1e9, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+                           "sample": "one SSP-RK3 step of the same workload at 512 x 512 cells, FP64 C oracle, one thread"},
             "hbm_frac": v * (128.0 / 3 + 8) / peak, "peak_gbs": peak, "peak_kind": kind,
             "traffic_bytes_per_cell": None if rec is None else rec["dram_bytes_per_cell_per_launch"],
             "issue_ceiling": issue_ceiling(2070.0, "stage_kernel_curvilinear_record.json", 128.0 / 3 + 8)}
