@@ -854,7 +854,13 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
     if (a.rate_zero && blockIdx.x == 0)
         for (int g = threadIdx.x; g < a.ngrids; g += NT) a.rate_zero[g] = 0ull;
 
-    double acc_s[4] = {0.0, 0.0, 0.0, 0.0}, acc_m[4] = {0.0, 0.0, 0.0, 0.0};
+    // MODE_NORM: each thread's FP64 sums of R^2 [k] and maxima of |R| [4 + k] in dynamic shared
+    // memory (slot k * NT + thread; only norm launches ask for it), rather than in sixteen
+    // registers that every launch would hold
+    extern __shared__ __align__(16) unsigned char norm_smem[];
+    double *const nacc = reinterpret_cast<double *>(norm_smem) + threadIdx.x;
+    if (a.mode == MODE_NORM)
+        for (int k = 0; k < 8; ++k) nacc[k * NT] = 0.0;
 
     // Each warp takes unit tile_lo + warp first, then (dynamic scheduling) the next unclaimed
     // one, in the order of the unit table (whole-batch launches: by decreasing height), so that
@@ -1156,8 +1162,8 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     } else if (!solid) {
                         for (int k = 0; k < 4; ++k) {
                             const double rk = (double)(D[k] * sc);
-                            acc_s[k] = fma(rk, rk, acc_s[k]);
-                            acc_m[k] = fmax(acc_m[k], fabs(rk));
+                            nacc[k * NT] = fma(rk, rk, nacc[k * NT]);
+                            nacc[(4 + k) * NT] = fmax(nacc[(4 + k) * NT], fabs(rk));
                         }
                     }
                 }
@@ -1197,7 +1203,7 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
         // Fixed-order block reduction of the FP64 partials: warp shuffles, then warp 0.
         __shared__ double wred[NT / 32][8];
         double v[8];
-        for (int k = 0; k < 4; ++k) { v[k] = acc_s[k]; v[4 + k] = acc_m[k]; }
+        for (int k = 0; k < 8; ++k) v[k] = nacc[k * NT];
         for (int o = 16; o > 0; o >>= 1)
             for (int k = 0; k < 8; ++k) {
                 const double x = __shfl_xor_sync(0xffffffffu, v[k], o);
@@ -1361,7 +1367,8 @@ template <typename T, bool MUSCL, bool CURV, bool WALLS, bool ABL = false> struc
     static constexpr int NT = STAGE_THREADS;
     static cudaError_t launch(const StageArgs<T> &a, int nblocks, cudaStream_t s)
     {
-        stage_kernel<T, MUSCL, CURV, WALLS, NT, ABL><<<nblocks, NT, 0, s>>>(a);
+        const size_t smem = a.mode == MODE_NORM ? 8 * NT * sizeof(double) : 0;   // (the norm accumulators)
+        stage_kernel<T, MUSCL, CURV, WALLS, NT, ABL><<<nblocks, NT, smem, s>>>(a);
         return cudaGetLastError();
     }
     static int occupancy()

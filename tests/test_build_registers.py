@@ -1,8 +1,11 @@
-"""Register budget of the FP32 stage kernels (nvcc cross-compiles here; no GPU needed): none of
-them spills to local memory. Their occupancy is set by registers (one-warp CTAs: 128 registers
-give 16 warps per SM, 168 give 12), and a spill in the loop body costs more than it saves (a
-56-byte spill that crept in through a rewritten address expression cost the benchmark batch's
-kernel its budget), so a change that makes one spill fails here before it reaches a GPU."""
+"""Register budget of the FP32 stage kernels (nvcc cross-compiles here; no GPU needed). Their
+occupancy is set by registers (one-warp CTAs: 128 registers give 16 warps per SM, 168 give 12).
+The first-order Cartesian kernels (the benchmark batch's family) must not spill: a 56-byte spill
+that crept in through a rewritten address expression once cost that kernel its budget. The
+reconstructing and curvilinear kernels are held to 128 registers too, where the 4096^2 warped
+step measured 10 % faster with 16 warps per SM and 60 bytes of spills than with 12 warps and
+none; their spills must stay within that measured bound, so that a change that grows them fails
+here before it reaches a GPU."""
 import os
 import re
 import subprocess
@@ -27,5 +30,7 @@ def test_fp32_stage_kernels_do_not_spill():
         m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
         if m and kernel and "stage_kernelIf" in kernel:
             seen += 1
-            assert m.group(1) == "0" and m.group(2) == "0", (kernel, line)
+            first_order_cartesian = "stage_kernelIfLb0ELb0E" in kernel
+            bound = 0 if first_order_cartesian else 64
+            assert int(m.group(1)) <= bound and int(m.group(2)) <= bound, (kernel, line)
     assert seen >= 8, r.stderr[-2000:]
