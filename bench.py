@@ -300,20 +300,24 @@ def warped_step_speed(P, torch, steps=20):
     v = spec.ncells * 3 / (ms * 1e-3) / 1e9
     peak, kind = peaks()
     rec = traffic_record("stage_kernel_curvilinear_record.json")
-    # the FP64 CPU oracle on the same workload at 512 x 512 (one SSP-RK3 step, one thread)
-    import oracle
-    oracle.build()
-    s2, U2 = W.warped_step(512, 512)
-    t0 = time.perf_counter()
-    oracle.OracleGrid(s2).step(U2, cfl=0.5)
-    t_orc = time.perf_counter() - t0
     return {"workload": "warped step 4096x4096 FP32, MUSCL van Leer, solid block, walls/inflow/outflow",
             "gcell_updates_per_s_per_stage": v, "ms_per_step": ms,
-            "cpu_oracle": {"value": s2.ncells * 3 / t_orc / 1e9, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
-                           "sample": "one SSP-RK3 step of the same workload at 512 x 512 cells, FP64 C oracle, one thread"},
             "hbm_frac": v * (128.0 / 3 + 8) / peak, "peak_gbs": peak, "peak_kind": kind,
             "traffic_bytes_per_cell": None if rec is None else rec["dram_bytes_per_cell_per_launch"],
             "issue_ceiling": issue_ceiling(2070.0, "stage_kernel_curvilinear_record.json", 128.0 / 3 + 8)}
+
+
+def cpu_baseline_curvilinear():
+    """The FP64 CPU oracle, one thread, on the curvilinear workload (warped step, MUSCL van Leer,
+    solid block) at 512 x 512 cells for one SSP-RK3 step: the CPU rate beside the 4096^2 line."""
+    import oracle
+    oracle.build()
+    spec, U = W.warped_step(512, 512)
+    t0 = time.perf_counter()
+    oracle.OracleGrid(spec).step(U, cfl=0.5)
+    t = time.perf_counter() - t0
+    return {"value": spec.ncells * 3 / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one SSP-RK3 step of the warped-step workload at 512 x 512 cells, FP64 C oracle, one thread"}
 
 
 def three_d_speed(P, torch, n=256, nscal=1, steps=20):
@@ -598,11 +602,13 @@ def run_ours(args):
     if rank == 0:
         cpu_v, cpu_sample, cpu_all = (None, None, None)
         vs_oracle = None
+        curv_oracle = None
         if world == 1 and not args.no_cpu:
             cpu_v, cpu_sample = cpu_baseline(specs, states, steps=1, budget_s=args.cpu_budget)
             cpu_all = cpu_baseline_all_cores(rank_seed(rank), args.grids, args.cpu_budget)
             if not args.no_extra:
                 vs_oracle = oracle_comparison(P)
+                curv_oracle = cpu_baseline_curvilinear()
         traffic = measured_traffic(ncells)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -624,6 +630,7 @@ def run_ours(args):
                 "sample": f"FP64 C oracle as independent processes, one per core, each stepping its share of "
                           f"the same batch's grids for {args.cpu_budget:.0f} s",
                 "single_core": {"value": cpu_v, "cores": 1, "sample": cpu_sample},
+                "curvilinear_single_core": curv_oracle,
                 "gpu_vs_oracle": vs_oracle},
             "e2e": e2e,
             "gpu_launches": launches,
