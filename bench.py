@@ -320,6 +320,27 @@ def cpu_baseline_curvilinear():
             "sample": "one SSP-RK3 step of the warped-step workload at 512 x 512 cells, FP64 C oracle, one thread"}
 
 
+def cpu_baseline_small_configs():
+    """The FP64 CPU oracle, one thread, on the small paper-scale workloads of `small_configs`:
+    ms per SSP-RK3 step (one step each, the same settings as the GPU measurement)."""
+    import oracle
+    oracle.build()
+    cases = [("vortex_64_fp64", W.isentropic_vortex(64), dict()),
+             ("gresho_256", W.gresho(256, mach=0.01), dict()),
+             ("quirk_800x20", W.quirk(800, 20, eps_y=1e-6), dict(cfl=0.25)),
+             ("cylinder_ogrid_100x72", W.cylinder_ogrid(mach=0.1), dict()),
+             ("blunt_body_160x20", W.cylinder_blunt(), dict(dt_fixed=1e-5)),
+             ("corner_400x400", W.supersonic_corner(400), dict(dt_fixed=2e-5)),
+             ("wedge_dmr_800x200", W.wedge_dmr(800, 200), dict(dt_fixed=2e-5))]
+    out = {}
+    for name, (spec, U), kw in cases:
+        g = oracle.OracleGrid(spec)
+        t0 = time.perf_counter()
+        g.step(U, **kw)
+        out[name] = {"ms_per_step": (time.perf_counter() - t0) * 1e3, "cores": 1}
+    return out
+
+
 def three_d_speed(P, torch, n=256, nscal=1, steps=20):
     """The 3D path (include/roeam3.h): Taylor-Green vortex on n^3 cells, FP32, one passive
     scalar, first order. Algorithmic bytes per cell and stage: (5 + nscal) 4-byte variables read
@@ -602,13 +623,14 @@ def run_ours(args):
     if rank == 0:
         cpu_v, cpu_sample, cpu_all = (None, None, None)
         vs_oracle = None
-        curv_oracle = None
+        curv_oracle = small_oracle = None
         if world == 1 and not args.no_cpu:
             cpu_v, cpu_sample = cpu_baseline(specs, states, steps=1, budget_s=args.cpu_budget)
             cpu_all = cpu_baseline_all_cores(rank_seed(rank), args.grids, args.cpu_budget)
             if not args.no_extra:
                 vs_oracle = oracle_comparison(P)
                 curv_oracle = cpu_baseline_curvilinear()
+                small_oracle = cpu_baseline_small_configs()
         traffic = measured_traffic(ncells)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -631,6 +653,7 @@ def run_ours(args):
                           f"the same batch's grids for {args.cpu_budget:.0f} s",
                 "single_core": {"value": cpu_v, "cores": 1, "sample": cpu_sample},
                 "curvilinear_single_core": curv_oracle,
+                "small_configs_single_core": small_oracle,
                 "gpu_vs_oracle": vs_oracle},
             "e2e": e2e,
             "gpu_launches": launches,
