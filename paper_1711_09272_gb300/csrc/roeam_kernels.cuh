@@ -1066,11 +1066,10 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 // where a reconstruction within rounding of zero is decided in FP64 (the
                 // reconstruction's bounds depend only on the face's two cells)
                 if (!scalar) {
+                    // (the faces' Eq. 97 ratios min/max of rho and p, already at hand for the
+                    //  detector, say whether the jump is 1e5 or more)
                     const T eps = T(1e-5);
-                    const bool marginal =
-                        (fx.A.r < eps * fx.B.r) || (fx.B.r < eps * fx.A.r) || (fx.A.p < eps * fx.B.p) ||
-                        (fx.B.p < eps * fx.A.p) || (fy.A.r < eps * fy.B.r) || (fy.B.r < eps * fy.A.r) ||
-                        (fy.A.p < eps * fy.B.p) || (fy.B.p < eps * fy.A.p);
+                    const bool marginal = Px[H] < eps || Py[H - 1] < eps;
                     scalar = __any_sync(0xffffffffu, marginal);
                 }
             }
