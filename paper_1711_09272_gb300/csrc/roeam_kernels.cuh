@@ -972,16 +972,6 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                 const int x = j * R.pitch + i;
                 for (int k = 0; k < 4; ++k) Un_next[k] = *DBG_LD(R, DB_UN, R.un + (x + k * R.plane));
             }
-            // U^(k) of row j-1 for this iteration's epilogue, issued before the faces (the
-            // reconstructing curvilinear kernel, which is latency-bound: +2.4 %; the others
-            // measured slower with it and read it again in the epilogue)
-            T Uk[4] = {T(0), T(0), T(0), T(0)};
-            if constexpr (MUSCL && CURV) {
-                if (stage_mode && out_lane && j > j0) {
-                    const int x = (j - 1) * R.pitch + i;
-                    for (int k = 0; k < 4; ++k) Uk[k] = __ldg(DBG_LD(R, DB_SRC, R.src + x + k * R.plane));
-                }
-            }
 
             // ---- the two faces of this lane: west x-face of row j (cells lane-1 | lane) and
             //      the y-face between rows j-1 and j (window H-1 | H)
@@ -1071,6 +1061,18 @@ __global__ void __launch_bounds__(NT, (stage_min_blocks<T, MUSCL, CURV, ABL>()))
                     const T eps = T(1e-5);
                     const bool marginal = Px[H] < eps || Py[H - 1] < eps;
                     scalar = __any_sync(0xffffffffu, marginal);
+                }
+            }
+            // U^(k) of row j-1 for this iteration's epilogue, issued just before the faces are
+            // evaluated (the reconstructing curvilinear kernel, which is latency-bound: +2.4 %
+            // over the epilogue read when issued at the top of the iteration, +2 % more and 36
+            // instead of 60 bytes of spills here, after the slopes and the screens; the other
+            // kernels measured slower with it and read it again in the epilogue)
+            T Uk[4] = {T(0), T(0), T(0), T(0)};
+            if constexpr (MUSCL && CURV) {
+                if (stage_mode && out_lane && j > j0) {
+                    const int x = (j - 1) * R.pitch + i;
+                    for (int k = 0; k < 4; ++k) Uk[k] = __ldg(DBG_LD(R, DB_SRC, R.src + x + k * R.plane));
                 }
             }
             if (scalar) {
