@@ -129,13 +129,17 @@ struct roeam_grid {
 // batch with float32 host arrays).
 static const double PIPE_SHARES[] = {1, 2, 3, 4, 4, 4, 4, 3, 2, 1};
 
+// Shortest segment height the halving below goes to (a grid's segments differ by at most one
+// row, so where its rows do not divide evenly some come out one row shorter).
+constexpr int MIN_SEGMENT_ROWS = 2;
+
 namespace {
 
 // Work units of the stage kernel for shape `cfg`: every grid is cut into strips of
 // 32 - 2H interior columns and into ceil(nj / ty) segments of nearly equal height. A batch
 // too small to give every resident warp a unit (a single grid of a few thousand cells, like
-// the paper's test cases) gets shorter segments, down to 4 rows: each segment re-reads H + 1
-// rows above its first, but the rows are swept by many more warps at once. Units are stored
+// the paper's test cases) gets shorter segments, down to MIN_SEGMENT_ROWS: each segment
+// re-reads H + 1 rows above its first, but the rows are swept by many more warps at once. Units are stored
 // grouped by grid (for launches over one grid) and, for whole-batch launches, ordered by
 // decreasing height so that the static round-robin over warps stays balanced.
 roeam_status setup_tiles(roeam_grid *g, int cfg)
@@ -151,8 +155,8 @@ roeam_status setup_tiles(roeam_grid *g, int cfg)
     for (;;) {
         long long units = 0;
         for (const GridDev &G : g->hg) units += (long long)((G.ni + width - 1) / width) * ((G.nj + ty - 1) / ty);
-        if (units >= warps || ty <= 4) break;
-        ty = std::max(4, ty / 2);
+        if (units >= warps || ty <= MIN_SEGMENT_ROWS) break;
+        ty = std::max(MIN_SEGMENT_ROWS, ty / 2);
     }
     // A single grid has units of one size, so a launch takes ceil(units / warps) rounds of them:
     // its segment count is raised by up to a quarter where that fills the last round better
@@ -254,7 +258,7 @@ roeam_status setup_tiles(roeam_grid *g, int cfg)
 }
 
 // roeam_step_host's unit table: the units of every chunk of grids, cut with the current tile
-// shape's segment height halved (down to 4 rows) until the chunk alone has a unit for every
+// shape's segment height halved (down to MIN_SEGMENT_ROWS) until the chunk alone has a unit for every
 // resident warp, ordered by decreasing height within the chunk.
 roeam_status setup_pipe_units(roeam_grid *g, const std::vector<std::pair<int, int>> &chunks)
 {
@@ -270,8 +274,8 @@ roeam_status setup_pipe_units(roeam_grid *g, const std::vector<std::pair<int, in
             long long units = 0;
             for (int k = ch.first; k < ch.second; ++k)
                 units += (long long)((g->hg[k].ni + width - 1) / width) * ((g->hg[k].nj + ty - 1) / ty);
-            if (units >= warps || ty <= 4) break;
-            ty = std::max(4, ty / 2);
+            if (units >= warps || ty <= MIN_SEGMENT_ROWS) break;
+            ty = std::max(MIN_SEGMENT_ROWS, ty / 2);
         }
         const size_t b0 = up.size();
         for (int k = ch.first; k < ch.second; ++k) {

@@ -346,7 +346,7 @@ def test_step_host_chunking_over_grid_counts(count):
 @pytest.mark.parametrize("shape", [(4, 4), (5, 7), (31, 4), (33, 5), (4, 65), (61, 6), (29, 129)])
 def test_tiny_and_tile_edge_grids(shape, prec, cfg):
     """The smallest grids and sizes at the strip / segment edges (30 or 28 written columns per
-    strip, segments of 16 to 128 rows, halved down to 4 rows for a single small grid):
+    strip, segments of 16 to 128 rows, halved down to 2 rows for a single small grid):
     periodic and wall/inflow/outflow, first order and van Leer, every work-unit shape."""
     ni, nj = shape
     for bc, recon in (((W.PERIODIC,) * 4, 0), ((W.INFLOW, W.OUTFLOW, W.WALL, W.WALL), 2)):
