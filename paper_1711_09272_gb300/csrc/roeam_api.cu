@@ -156,7 +156,20 @@ roeam_status setup_tiles(roeam_grid *g, int cfg)
         long long units = 0;
         for (const GridDev &G : g->hg) units += (long long)((G.ni + width - 1) / width) * ((G.nj + ty - 1) / ty);
         if (units >= warps || ty <= MIN_SEGMENT_ROWS) break;
-        ty = std::max(MIN_SEGMENT_ROWS, ty / 2);
+        const int next = std::max(MIN_SEGMENT_ROWS, ty / 2);
+        if (next < 4) {
+            // Below 4 rows a unit re-reads about as many warm-up rows as it writes: halve there
+            // only while the units still fit one round of the resident warps (a single grid's
+            // segment count may drop by an eighth below to make them fit). The 400^2 corner's
+            // 2-row units took two rounds and stepped slower than its 4-row ones.
+            long long fit = 0;
+            for (const GridDev &G : g->hg) {
+                const long long nty = (G.nj + next - 1) / next;
+                fit += (long long)((G.ni + width - 1) / width) * (g->count == 1 ? nty - nty / 8 : nty);
+            }
+            if (fit > warps) break;
+        }
+        ty = next;
     }
     // A single grid has units of one size, so a launch takes ceil(units / warps) rounds of them:
     // its segment count is raised by up to a quarter where that fills the last round better
@@ -275,7 +288,15 @@ roeam_status setup_pipe_units(roeam_grid *g, const std::vector<std::pair<int, in
             for (int k = ch.first; k < ch.second; ++k)
                 units += (long long)((g->hg[k].ni + width - 1) / width) * ((g->hg[k].nj + ty - 1) / ty);
             if (units >= warps || ty <= MIN_SEGMENT_ROWS) break;
-            ty = std::max(MIN_SEGMENT_ROWS, ty / 2);
+            const int next = std::max(MIN_SEGMENT_ROWS, ty / 2);
+            if (next < 4) {
+                // (below 4 rows only while the chunk's units still fit one round, as above)
+                long long fit = 0;
+                for (int k = ch.first; k < ch.second; ++k)
+                    fit += (long long)((g->hg[k].ni + width - 1) / width) * ((g->hg[k].nj + next - 1) / next);
+                if (fit > warps) break;
+            }
+            ty = next;
         }
         const size_t b0 = up.size();
         for (int k = ch.first; k < ch.second; ++k) {
