@@ -871,6 +871,8 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(ROEAM_E_ARG, "device %d not present (%d devices)", device, ndev);
     CUDA_TRY(cudaSetDevice(device));
+    int num_sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
 
     roeam_grid *g = new roeam_grid();
     g->device = device;
@@ -880,7 +882,7 @@ roeam_status roeam_create_grid(int count, const roeam_grid_desc *descs, int devi
     g->esize = g->precision == 32 ? 4 : 8;
     g->muscl = descs[0].p.recon > 0;
     g->curv = descs[0].xv != nullptr;
-    CUDA_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, device));
+    g->num_sms = num_sms;
     g->hg.resize(count);
     g->state_set.assign(count, 0);
     long long off = 0, voff = 0, soff = 0, poff = 0;
