@@ -4,8 +4,10 @@ The first-order Cartesian kernels (the benchmark batch's family) must not spill:
 that crept in through a rewritten address expression once cost that kernel its budget. The
 reconstructing and curvilinear kernels are held to 128 registers too, where the 4096^2 warped
 step measured 10 % faster with 16 warps per SM and 60 bytes of spills than with 12 warps and
-none; their spills must stay within that measured bound, so that a change that grows them fails
-here before it reaches a GPU. The 3D FP32 kernel's spills are bounded the same way."""
+none (they spill at most 48 bytes now: 36 in the warped step's kernel since its U^(k) load moved
+to just before the faces); their spills must stay within that bound, so that a change that
+grows them fails here before it reaches a GPU. The 3D FP32 kernel's spills are bounded the same
+way."""
 import os
 import re
 import subprocess
@@ -31,7 +33,7 @@ def test_fp32_stage_kernels_do_not_spill():
         if m and kernel and "stage_kernelIf" in kernel:
             seen += 1
             first_order_cartesian = "stage_kernelIfLb0ELb0E" in kernel
-            bound = 0 if first_order_cartesian else 64
+            bound = 0 if first_order_cartesian else 48
             assert int(m.group(1)) <= bound and int(m.group(2)) <= bound, (kernel, line)
     assert seen >= 8, r.stderr[-2000:]
 
