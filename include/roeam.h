@@ -282,8 +282,8 @@ roeam_status roeam_flux_residual_noalloc(roeam_grid *g, int grid_idx, double *re
  * 128 and 256 rows and let warps claim units dynamically in the order of the unit table
  * (tallest first); shapes 5-9 are the same heights with a static round robin of units over
  * warps. (Kernels that do not claim units dynamically treat 0-4 as 5-9; a batch too small to
- * give every resident warp a unit halves the height down to 2 rows.) Results are bit-identical
- * across shapes. */
+ * give every resident warp a unit halves the height, down to 4 rows, and on to 2 rows while the
+ * units still fit one round of the resident warps.) Results are bit-identical across shapes. */
 int roeam_tile_config_count(void);
 
 /* Describes tile shape `cfg`: strip width tx, segment height ty (cells) and threads per CTA. */
